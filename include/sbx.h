@@ -1,0 +1,206 @@
+/*
+ * sbx.h -- C ABI of the GB300 explicit octree-SBFEM solver.
+ *
+ * One library call sequence mirrors the problem statement of the paper's
+ * serial solver (Algorithm 1 and Table "Data structure of explicit solver"):
+ *
+ *   sbx_create        -- bind a CUDA device and stream
+ *   set_patterns      -- master-cell stiffness K_p and lumped mass (Table: K_e, M_e)
+ *   mesh_upload       -- cells: pattern T, transform, DOF vector V, edge length S,
+ *                        modulus, density; Dirichlet DOFs Gamma_D (Alg. 1 lines 1-6)
+ *   set_load          -- point loads Gamma_N with a time function (Sec. 5, Eqs.
+ *                        Ricker, Triangle, Lamb)
+ *   set_initial       -- U_0, Udot_0 and the fictitious U_-1 (Eq. D0)
+ *   step_n            -- n central-difference steps (Alg. 1 lines 8-20;
+ *                        Eqs. Rintep, DnMdiag)
+ *   read_field / write_field -- state in and out (checkpoint / resume)
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: SBX_OK (0) or one of the
+ *     SBX_E* codes below; sbx_last_error() gives a one-line message.  No
+ *     C++ exception and no abort crosses this boundary.
+ *   - Array arguments may point to host memory (pageable or pinned) or to
+ *     device memory of the context's device; the library tells them apart
+ *     with cudaPointerGetAttributes.  The library copies every input into
+ *     memory it owns; the caller keeps ownership of its buffers, which may
+ *     be freed as soon as the call returns.
+ *   - Work is enqueued on the stream given to sbx_create.  step_n and
+ *     set_initial are asynchronous with respect to the host; read_field,
+ *     sbx_sync and sbx_destroy synchronise that stream.
+ *   - Node ids are 0-based; DOF = 3 * node + direction (x, y, z).  With
+ *     n_rhs = B > 1 load cases, a field is laid out [node][3][B]
+ *     (entry (3 * node + d) * B + b).
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - Unless stated otherwise lengths are element counts, not bytes.
+ */
+#ifndef SBX_H
+#define SBX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbx_ctx sbx_ctx;
+
+/* status codes */
+#define SBX_OK          0
+#define SBX_EINVAL      1  /* an argument is out of range or inconsistent     */
+#define SBX_ENOMEM      2  /* device or host allocation failed                */
+#define SBX_ECUDA       3  /* a CUDA runtime call failed                      */
+#define SBX_ENONFINITE  4  /* a NaN/Inf appeared in the displacement field    */
+#define SBX_ETIMEOUT    5  /* a bounded device-side wait gave up              */
+#define SBX_ESTATE      6  /* call out of order (e.g. step before mesh_upload) */
+
+/* precision modes of mesh_upload (the displacement history is FP64 in all) */
+#define SBX_PREC_FP64   0  /* K_p u_e in FP64 (DFMA)                           */
+#define SBX_PREC_MIXED  1  /* K_p u_e as three TF32 tensor-core products of
+                              split operands, FP32 accumulation (tcgen05)     */
+#define SBX_PREC_FP32   2  /* K_p u_e in FP32 (FFMA), FP64 scale and update   */
+
+/* fields of read_field / write_field */
+#define SBX_U_N         0  /* U_n, displacement at the current step           */
+#define SBX_U_NM1       1  /* U_{n-1}                                         */
+#define SBX_F_INT       2  /* R_int of the last evaluated step (read only)    */
+#define SBX_MASS        3  /* lumped global diagonal mass M_diag (read only)  */
+
+/* wavelets of set_load */
+#define SBX_WAVE_RICKER     0  /* Eq. (Ricker)                                */
+#define SBX_WAVE_TRIANGLE   1  /* Eq. (Triangle)                              */
+#define SBX_WAVE_SINE_BURST 2  /* Eq. (Lamb), Hann-windowed sine burst        */
+
+/*
+ * sbx_create: bind `device` and a CUDA stream.
+ *   cuda_stream: a cudaStream_t of that device, or NULL for a stream the
+ *   library creates (and destroys in sbx_destroy).
+ *   Errors: SBX_EINVAL (out == NULL, bad device), SBX_ECUDA, SBX_ENOMEM.
+ */
+int sbx_create(sbx_ctx **out, int device, void *cuda_stream);
+
+/* sbx_destroy: synchronise the stream and free everything (NULL is a no-op). */
+int sbx_destroy(sbx_ctx *ctx);
+
+/* One-line description of the last error of this context ("" if none).
+ * The string lives until the next call on the context. */
+const char *sbx_last_error(const sbx_ctx *ctx);
+
+/* Block until the context's stream is idle; reports a pending
+ * non-finite-field flag as SBX_ENONFINITE. */
+int sbx_sync(sbx_ctx *ctx);
+
+/*
+ * set_patterns: the master cells of Sec. 3.2.2-3.2.3 (Table: K_e, M_e).
+ *   n_patterns        number of master cells P (1 .. 144).
+ *   n_nodes[P]        nodes n_p of master p, 8 <= n_p <= 26; m_p = 3 n_p.
+ *   K_packed          the P stiffness matrices K_p for unit edge length and
+ *                     E = 1 (Eq. KM_scale), each m_p x m_p row-major FP64,
+ *                     concatenated in pattern order (sum m_p^2 doubles).
+ *                     Must be symmetric to 1e-12 relative.
+ *   Mlump_packed      the P lumped masses (Sec. 3.3) for unit edge length and
+ *                     rho = 1, m_p doubles each, DOF order 3 * node + dir.
+ *   Must be called before mesh_upload; calling it again invalidates the mesh.
+ *   Errors: SBX_EINVAL (sizes, asymmetric K, non-positive mass), SBX_ENOMEM.
+ */
+int set_patterns(sbx_ctx *ctx, int n_patterns, const int32_t *n_nodes,
+                 const double *K_packed, const double *Mlump_packed);
+
+/*
+ * mesh_upload: the octree mesh of Alg. 1 lines 1-6 (Table: V, T, S, M_diag,
+ * Gamma_D).  Builds the lumped global mass M_diag = sum_e rho_e h_e^3 M_p(e)
+ * (in cell components) and allocates the state (U_n = U_{n-1} = 0).
+ *   n_nodes, n_cells  N and C.
+ *   cell_pattern[C]   master index p of each cell (into set_patterns' list).
+ *   cell_sym[C]       transform op in [0, 48): op = 8 * perm_index + sign_bits
+ *                     with the permutations of (0,1,2) in lexicographic order;
+ *                     node by node u_master[r] = (-1)^{bit r} u_cell[perm[r]]
+ *                     and f_cell = Q^T f_master (Sec. 3.2.2).
+ *   cell_ptr[C+1]     offsets into cell_nodes; cell_ptr[e+1]-cell_ptr[e] = n_p.
+ *   cell_nodes[]      node ids of each cell in MASTER node order (the master's
+ *                     present slots in increasing slot order), i.e. the DOF
+ *                     vector V already arranged for the master (Sec. 3.4).
+ *   h[C], E[C], rho[C] edge length, Young's modulus, density (all > 0).
+ *                     K_e = E_e h_e T^T K_p T (Eq. KM_scale).
+ *   n_fixed, fixed_dofs[n_fixed]  Dirichlet DOFs held at zero (Gamma_D).
+ *   n_rhs             number of load cases B advanced together (1 = plain).
+ *   precision_mode    SBX_PREC_*.
+ *   Cells are processed grouped by pattern; within a pattern the given order
+ *   is kept (pass Morton order for locality).
+ *   Errors: SBX_ESTATE (no patterns), SBX_EINVAL (ids out of range, node count
+ *   mismatch, non-positive h/E/rho), SBX_ENOMEM.
+ */
+int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells,
+                const int32_t *cell_pattern, const uint8_t *cell_sym,
+                const int64_t *cell_ptr, const int32_t *cell_nodes,
+                const double *h, const double *E, const double *rho,
+                int64_t n_fixed, const int64_t *fixed_dofs,
+                int n_rhs, int precision_mode);
+
+/*
+ * set_load: point loads (Gamma_N) R_ext(t) = sum_k P0_k P_k(t) dir_k at node_k
+ * for load case rhs_k (Sec. 5 load functions).
+ *   n_src             number of point loads K (0 clears the loads).
+ *   node[K], dir3[3K] node id and direction vector (used as given).
+ *   rhs[K]            load case in [0, n_rhs), or NULL for all 0.
+ *   wavelet           SBX_WAVE_* (one kind for all loads of the call).
+ *   t1[K], P0[K]      time parameter and peak of each load; ncyc[K] the
+ *                     number of cycles of a sine burst (NULL otherwise).
+ *   The load enters step n at t_n = n dt.
+ *   Errors: SBX_ESTATE (no mesh), SBX_EINVAL.
+ */
+int set_load(sbx_ctx *ctx, int n_src, const int64_t *node, const double *dir3,
+             const int32_t *rhs, int wavelet, const double *t1,
+             const double *P0, const double *ncyc);
+
+/*
+ * set_initial: U_0 and Udot_0 (NULL = zero), then the fictitious
+ * U_-1 = U_0 - dt Udot_0 + dt^2/2 Uddot_0 with
+ * Uddot_0 = M^-1 (R_ext(0) - K U_0) - alpha Udot_0 (Eq. D0).  Resets the step
+ * index to 0.  Fixed DOFs are set to zero.  Lengths: 3 N n_rhs.
+ *   Errors: SBX_ESTATE (no mesh), SBX_EINVAL (dt <= 0), SBX_ECUDA.
+ */
+int set_initial(sbx_ctx *ctx, const double *u0, const double *v0,
+                double dt, double alpha);
+
+/*
+ * step_n: n_steps steps of Eq. (DnMdiag):
+ *   U_{n+1} = [dt^2 M^-1 (R_ext(t_n) - R_int(U_n)) + 2 U_n
+ *              - (1 - alpha dt / 2) U_{n-1}] / (1 + alpha dt / 2),
+ * R_int = sum_p K_p [U_p1 ... U_pk] diag(S) assembled through V (Eq. Rintep).
+ *   Asynchronous.  dt > 0, alpha >= 0.  A NaN/Inf produced in the field sets
+ *   a flag that the next synchronising call reports as SBX_ENONFINITE.
+ *   Errors: SBX_ESTATE, SBX_EINVAL, SBX_ECUDA.
+ */
+int step_n(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha);
+
+/* Current step index n (the state holds U_n and U_{n-1}). */
+int sbx_get_step(sbx_ctx *ctx, int64_t *n_out);
+/* Set the step index, e.g. after write_field when resuming. */
+int sbx_set_step(sbx_ctx *ctx, int64_t n);
+
+/*
+ * read_field: copy field `which` (SBX_U_N, SBX_U_NM1, SBX_F_INT, SBX_MASS)
+ * into out[len]; len must equal 3 N n_rhs (3 N for SBX_MASS).  Synchronises
+ * the stream.  SBX_F_INT holds R_int - R_ext of the last step.
+ *   Errors: SBX_ESTATE, SBX_EINVAL (len, which), SBX_ENONFINITE, SBX_ECUDA.
+ */
+int read_field(sbx_ctx *ctx, int which, double *out, int64_t len);
+
+/* write_field: overwrite SBX_U_N or SBX_U_NM1 from in[len] (resume). */
+int write_field(sbx_ctx *ctx, int which, const double *in, int64_t len);
+
+/*
+ * sbx_profile: diagnostics.  Runs n_steps ordinary steps (same kernels and
+ * launch shapes as step_n, without graph replay), bracketing every kernel
+ * launch with CUDA events on the context stream, and returns the summed
+ * device time in milliseconds of the internal-force launches (*ms_force)
+ * and of the update launches (*ms_update).  Advances the state like step_n.
+ *   Errors: as step_n.
+ */
+int sbx_profile(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha,
+                double *ms_force, double *ms_update);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBX_H */

@@ -86,13 +86,26 @@ def global_K_bruteforce(mesh) -> sp.csr_matrix:
                          shape=(n, n))
 
 
+def _mask_groups(mesh):
+    """Cells grouped by hanging-node mask: {mask: cell indices}."""
+    masks = np.asarray(mesh.mask, np.int64)
+    order = np.argsort(masks, kind="stable")
+    uniq, first = np.unique(masks[order], return_index=True)
+    bounds = list(first) + [len(order)]
+    return {int(u): order[bounds[i]:bounds[i + 1]] for i, u in enumerate(uniq)}
+
+
 def lumped_mass(mesh) -> np.ndarray:
-    """Global diagonal mass M_diag (Algorithm 1, line 5)."""
+    """Global diagonal mass M_diag (Algorithm 1, line 5): sum over cells of
+    rho_e h_e^3 diag(T^T M_lump,p T), added in through each cell's DOFs."""
     M = np.zeros(mesh.n_dof)
-    for c in range(mesh.n_cells):
-        _, ML = cell_matrices_from_master(int(mesh.mask[c]), mesh.h[c], mesh.E[c],
-                                          mesh.rho[c], mesh.nu)
-        np.add.at(M, cell_dofs(mesh, c), ML)
+    for mask, cells in _mask_groups(mesh).items():
+        _, ML = cell_matrices_from_master(mask, 1.0, 1.0, 1.0, mesh.nu)
+        slots = np.array(cube.present_slots(mask))
+        nodes = mesh.slot_node[cells][:, slots].astype(np.int64)
+        dofs = (3 * nodes[:, :, None] + np.arange(3)[None, None, :]).reshape(len(cells), -1)
+        w = (mesh.rho[cells] * mesh.h[cells] ** 3)[:, None] * ML[None, :]
+        np.add.at(M, dofs.ravel(), w.ravel())
     return M
 
 
@@ -100,13 +113,10 @@ def critical_dt(mesh) -> float:
     """min over cells of sqrt(rho/E) h dt_cr(master) (Eqs. tcr, tcr_scale)."""
     canon_tab, _ = cube.canonical_table()
     best = np.inf
-    cache = {}
-    for c in range(mesh.n_cells):
-        p = int(canon_tab[int(mesh.mask[c])])
-        if p not in cache:
-            mc = sbfem.master_cell(p, mesh.nu)
-            cache[p] = sbfem.critical_dt(mc.K, mc.M_lump)
-        best = min(best, np.sqrt(mesh.rho[c] / mesh.E[c]) * mesh.h[c] * cache[p])
+    for mask, cells in _mask_groups(mesh).items():
+        mc = sbfem.master_cell(int(canon_tab[mask]), mesh.nu)
+        dtp = sbfem.critical_dt(mc.K, mc.M_lump)
+        best = min(best, float(np.min(np.sqrt(mesh.rho[cells] / mesh.E[cells]) * mesh.h[cells])) * dtp)
     return float(best)
 
 
@@ -119,32 +129,41 @@ def pattern_tables(mesh):
     which together spell out K_cell = s_e T^T K_p T entry by entry.
     """
     canon_tab, op_tab = cube.canonical_table()
-    pats = sorted(set(int(canon_tab[int(m)]) for m in mesh.mask))
+    masks = np.asarray(mesh.mask, np.int64)
+    pats = sorted(set(int(canon_tab[m]) for m in np.unique(masks)))
     pidx = {p: i for i, p in enumerate(pats)}
-    cell_pat = np.zeros(mesh.n_cells, np.int64)
-    ptr = [0]
-    dofs, tmap, comp, sign = [], [], [], []
-    for c in range(mesh.n_cells):
-        mask = int(mesh.mask[c])
+    C = mesh.n_cells
+    nper = np.array([len(cube.present_slots(int(m))) for m in range(4096)])[masks]
+    ptr = np.zeros(C + 1, np.int64)
+    np.cumsum(nper, out=ptr[1:])
+    cell_pat = np.zeros(C, np.int64)
+    tmap = np.zeros(ptr[-1], np.int64)
+    nodes_all = np.zeros(ptr[-1], np.int64)
+    comp = np.zeros((C, 3), np.int64)
+    sign = np.zeros((C, 3), np.int64)
+    for mask, cells in _mask_groups(mesh).items():
         canon, op = int(canon_tab[mask]), int(op_tab[mask])
-        cell_pat[c] = pidx[canon]
+        cell_pat[cells] = pidx[canon]
         Q = cube.all_ops()[op]
         pi = cube.slot_perm(op)
         cs = cube.present_slots(mask)
         ms = cube.present_slots(canon)
         mloc = {s: j for j, s in enumerate(ms)}
-        dofs.append(cell_dofs(mesh, c))
-        tmap.append([mloc[pi[s]] for s in cs])
+        tm = np.array([mloc[pi[s]] for s in cs], np.int64)
         # (T u)[3j + r] = sum_a Q[r, a] u[3i + a]  =>  cell component a maps to
         # master component r = the row where column a of Q is nonzero.
         cr = [int(np.nonzero(Q[:, a])[0][0]) for a in range(3)]
-        comp.append(cr)
-        sign.append([int(Q[cr[a], a]) for a in range(3)])
-        ptr.append(ptr[-1] + len(cs))
+        comp[cells] = cr
+        sign[cells] = [int(Q[cr[a], a]) for a in range(3)]
+        idx = (ptr[cells][:, None] + np.arange(len(cs))[None, :]).ravel()
+        tmap[idx] = np.tile(tm, len(cells))
+        nodes = mesh.slot_node[cells][:, np.array(cs)]
+        if (nodes < 0).any():
+            raise ValueError("mesh slot table disagrees with the face-centre rule")
+        nodes_all[idx] = nodes.ravel()
+    dofs = (3 * nodes_all[:, None] + np.arange(3)[None, :]).ravel()
     Ks = [sbfem.master_cell(p, mesh.nu).K for p in pats]
     MLs = [sbfem.master_cell(p, mesh.nu).M_lump for p in pats]
     return {"patterns": pats, "cell_pat": cell_pat, "scale": mesh.E * mesh.h,
-            "node_ptr": np.array(ptr, np.int64), "dofs": np.concatenate(dofs).astype(np.int64),
-            "tmap": np.concatenate(tmap).astype(np.int64),
-            "comp": np.array(comp, np.int64), "sign": np.array(sign, np.int64),
-            "K": Ks, "M_lump": MLs}
+            "node_ptr": ptr, "dofs": dofs.astype(np.int64), "tmap": tmap,
+            "comp": comp, "sign": sign, "K": Ks, "M_lump": MLs}

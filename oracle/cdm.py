@@ -85,11 +85,7 @@ def make_problem(mesh, dt=None, dt_factor=0.5, alpha=0.0, sources=None, rhs=0) -
     dt_factor * dt_cr (Eqs. tcr, tcr_scale).  Only sources of load case
     ``rhs`` are applied."""
     tab = assembly.pattern_tables(mesh)
-    M = np.zeros(mesh.n_dof)
-    for c in range(mesh.n_cells):
-        _, ML = assembly.cell_matrices_from_master(int(mesh.mask[c]), mesh.h[c], mesh.E[c],
-                                                   mesh.rho[c], mesh.nu)
-        np.add.at(M, assembly.cell_dofs(mesh, c), ML)
+    M = assembly.lumped_mass(mesh)
     if dt is None:
         dt = dt_factor * assembly.critical_dt(mesh)
     fixed = mesh.fixed_dofs()

@@ -1,0 +1,170 @@
+"""ctypes binding of the sbx C ABI (include/sbx.h): same names, marshalling only.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); the
+library decides host vs device from the pointer.  A non-zero status raises
+``SbxError`` with the library's message.  There is no fallback: if the
+compiled library is missing, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsbx.so")
+
+SBX_OK, SBX_EINVAL, SBX_ENOMEM, SBX_ECUDA, SBX_ENONFINITE, SBX_ETIMEOUT, SBX_ESTATE = range(7)
+SBX_PREC_FP64, SBX_PREC_MIXED, SBX_PREC_FP32 = 0, 1, 2
+SBX_U_N, SBX_U_NM1, SBX_F_INT, SBX_MASS = 0, 1, 2, 3
+SBX_WAVE_RICKER, SBX_WAVE_TRIANGLE, SBX_WAVE_SINE_BURST = 0, 1, 2
+STATUS_NAMES = {0: "SBX_OK", 1: "SBX_EINVAL", 2: "SBX_ENOMEM", 3: "SBX_ECUDA",
+                4: "SBX_ENONFINITE", 5: "SBX_ETIMEOUT", 6: "SBX_ESTATE"}
+
+# every symbol include/sbx.h declares
+EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patterns",
+           "mesh_upload", "set_load", "set_initial", "step_n", "sbx_get_step", "sbx_set_step",
+           "read_field", "write_field", "sbx_profile"]
+
+
+class SbxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, code), msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled library (build it first with ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("sbx CUDA library not built: %s (run paper_2103_09100_gb300.build)" % path)
+    lib = C.CDLL(path)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "sbx_create": [C.POINTER(vp), i32, vp],
+        "sbx_destroy": [vp],
+        "sbx_sync": [vp],
+        "set_patterns": [vp, i32, vp, vp, vp],
+        "mesh_upload": [vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, i64, vp, i32, i32],
+        "set_load": [vp, i32, vp, vp, vp, i32, vp, vp, vp],
+        "set_initial": [vp, vp, vp, dbl, dbl],
+        "step_n": [vp, i64, dbl, dbl],
+        "sbx_get_step": [vp, C.POINTER(i64)],
+        "sbx_set_step": [vp, i64],
+        "read_field": [vp, i32, vp, i64],
+        "write_field": [vp, i32, vp, i64],
+        "sbx_profile": [vp, i64, dbl, dbl, C.POINTER(dbl), C.POINTER(dbl)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.sbx_last_error.argtypes = [vp]
+    lib.sbx_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(a, dtype=None):
+    """Raw pointer of a numpy array / torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or not a.flags.c_contiguous:
+        raise ValueError("expected a C-contiguous numpy array")
+    if dtype is not None and a.dtype != dtype:
+        raise ValueError("expected dtype %s, got %s" % (dtype, a.dtype))
+    return C.c_void_p(a.ctypes.data)
+
+
+def _check(ctx, rc):
+    if rc != SBX_OK:
+        msg = load().sbx_last_error(ctx).decode() if ctx else ""
+        raise SbxError(rc, msg)
+
+
+def sbx_create(device: int = 0, stream: int | None = None):
+    lib = load()
+    h = C.c_void_p()
+    rc = lib.sbx_create(C.byref(h), device, C.c_void_p(stream) if stream else None)
+    if rc != SBX_OK:
+        raise SbxError(rc, "sbx_create failed")
+    return h
+
+
+def sbx_destroy(ctx):
+    _check(ctx, load().sbx_destroy(ctx))
+
+
+def sbx_last_error(ctx) -> str:
+    return load().sbx_last_error(ctx).decode()
+
+
+def sbx_sync(ctx):
+    _check(ctx, load().sbx_sync(ctx))
+
+
+def set_patterns(ctx, n_nodes, K_packed, Mlump_packed):
+    _check(ctx, load().set_patterns(ctx, len(n_nodes), _ptr(n_nodes, np.int32),
+                                    _ptr(K_packed, np.float64), _ptr(Mlump_packed, np.float64)))
+
+
+def mesh_upload(ctx, n_nodes, cell_pattern, cell_sym, cell_ptr, cell_nodes, h, E, rho,
+                fixed_dofs, n_rhs=1, precision_mode=SBX_PREC_FP64):
+    _check(ctx, load().mesh_upload(ctx, int(n_nodes), len(cell_pattern), _ptr(cell_pattern, np.int32),
+                                   _ptr(cell_sym, np.uint8), _ptr(cell_ptr, np.int64),
+                                   _ptr(cell_nodes, np.int32), _ptr(h, np.float64),
+                                   _ptr(E, np.float64), _ptr(rho, np.float64), len(fixed_dofs),
+                                   _ptr(fixed_dofs, np.int64), int(n_rhs), int(precision_mode)))
+
+
+def set_load(ctx, node, dir3, rhs, wavelet, t1, P0, ncyc=None):
+    _check(ctx, load().set_load(ctx, len(node), _ptr(node, np.int64), _ptr(dir3, np.float64),
+                                _ptr(rhs, np.int32), int(wavelet), _ptr(t1, np.float64),
+                                _ptr(P0, np.float64), _ptr(ncyc, np.float64)))
+
+
+def set_initial(ctx, u0, v0, dt, alpha=0.0):
+    _check(ctx, load().set_initial(ctx, _ptr(u0, np.float64), _ptr(v0, np.float64), float(dt),
+                                   float(alpha)))
+
+
+def step_n(ctx, n_steps, dt, alpha=0.0):
+    _check(ctx, load().step_n(ctx, int(n_steps), float(dt), float(alpha)))
+
+
+def sbx_get_step(ctx) -> int:
+    n = C.c_int64()
+    _check(ctx, load().sbx_get_step(ctx, C.byref(n)))
+    return n.value
+
+
+def sbx_set_step(ctx, n):
+    _check(ctx, load().sbx_set_step(ctx, int(n)))
+
+
+def read_field(ctx, which, out):
+    n = out.numel() if hasattr(out, "numel") else out.size
+    _check(ctx, load().read_field(ctx, int(which), _ptr(out, np.float64), int(n)))
+    return out
+
+
+def sbx_profile(ctx, n_steps, dt, alpha=0.0):
+    """(ms of all force launches, ms of all update launches) over n_steps."""
+    a, b = C.c_double(), C.c_double()
+    _check(ctx, load().sbx_profile(ctx, int(n_steps), float(dt), float(alpha), C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def write_field(ctx, which, src):
+    n = src.numel() if hasattr(src, "numel") else src.size
+    _check(ctx, load().write_field(ctx, int(which), _ptr(src, np.float64), int(n)))

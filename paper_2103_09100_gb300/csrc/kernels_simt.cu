@@ -1,0 +1,264 @@
+// SIMT kernels of the explicit step: element-by-element internal force
+// (gather -> K_p contraction -> signed-permutation scatter), the lumped-mass
+// central-difference update and the start-up of Eq. (D0).
+//
+// Internal force (Eqs. Rinte, Rintep): for each cell e of pattern p,
+//   u_m = T_e u_e            (node order already in master order; component
+//                             permutation and signs of the cell's op)
+//   f_m = s_e K_p u_m        (s_e = E_e h_e, Eq. KM_scale)
+//   R_int[V_e] += T_e^T f_m  (Sec. 3.2.2: back-transform with Q^-1 = Q^T)
+// One CTA handles a tile of up to SIMT_TILE cells of one pattern; K_p and
+// the gathered displacements live in shared memory; every thread owns one
+// cell and a strided subset of K_p's rows, so a warp reads one K_p entry as
+// a broadcast and 32 distinct displacement entries.
+#include <math.h>
+
+#include "sbx_internal.cuh"
+
+namespace sbx {
+
+__constant__ int8_t c_perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2},
+                                    {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+__device__ __forceinline__ int op_perm(int op, int r) { return c_perm[op >> 3][r]; }
+__device__ __forceinline__ double op_sign(int op, int r) { return ((op >> r) & 1) ? -1.0 : 1.0; }
+
+// Time functions of Sec. 5: Eqs. (Ricker), (Triangle), (Lamb).
+__device__ double wavelet(int kind, double t, double t1, double ncyc) {
+  if (kind == SBX_WAVE_RICKER) {
+    double tau = (t - t1) / (t1 / 5.0);
+    return (1.0 - tau * tau) * exp(-0.5 * tau * tau);
+  } else if (kind == SBX_WAVE_TRIANGLE) {
+    if (t < 0.0 || t > 2.0 * t1) return 0.0;
+    return 1.0 - fabs(t / t1 - 1.0);
+  } else {
+    if (t < 0.0 || t > t1) return 0.0;
+    double s = sin(M_PI * t / t1);
+    return sin(2.0 * M_PI * ncyc * t / t1) * s * s;
+  }
+}
+
+// f -= R_ext(t_n): called by one CTA of the force kernel.
+__device__ void add_external(const LoadTable L, const int64_t *d_step, double dt, double *f) {
+  if (L.n == 0) return;
+  double t = (double)(*d_step) * dt;
+  for (int l = threadIdx.x; l < L.n; l += blockDim.x)
+    atomicAdd(&f[L.dof[l]], -L.amp[l] * wavelet(L.kind[l], t, L.t1[l], L.ncyc[l]));
+}
+
+// T = double: FP64 DFMA contraction.
+// T = float : the gathered displacement minus its per-cell mean translation
+//             (computed in FP64; K_p annihilates translations) is rounded to
+//             FP32 and contracted with FP32 K_p in FFMA; the result is scaled
+//             by s_e and accumulated in FP64.
+template <typename T, int TC>
+__global__ void __launch_bounds__(256) k_force_simt(const Tile *__restrict__ tiles, MeshView M,
+                                                    const T *__restrict__ Kp,
+                                                    const double *__restrict__ u,
+                                                    double *__restrict__ f, LoadTable L,
+                                                    const int64_t *__restrict__ d_step, double dt) {
+  const Tile t = tiles[blockIdx.x];
+  const int p = t.pat;
+  const int m = M.pat_m[p];
+  const int n = m / 3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Ks = reinterpret_cast<T *>(smem_raw);
+  T *Us = Ks + m * m;
+  int32_t *Ns = reinterpret_cast<int32_t *>(Us + m * TC);
+  const T *Kg = Kp + M.koff[p];
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) Ks[i] = Kg[i];
+
+  const int64_t Cp = M.pat_ccount[p];
+  const int32_t *cn = M.conn + M.conn_off[p];
+  const int64_t gbase = M.pat_cstart[p] + t.cell0;
+  const int nc = t.ncell;
+
+  if constexpr (sizeof(T) == 8) {
+    for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+      const int k = idx / TC, c = idx % TC;
+      if (c < nc) {
+        const int32_t node = cn[(int64_t)k * Cp + t.cell0 + c];
+        const int op = M.sym[gbase + c];
+        const double *un = u + 3 * (int64_t)node;
+        const double v[3] = {un[0], un[1], un[2]};
+#pragma unroll
+        for (int r = 0; r < 3; ++r) Us[(3 * k + r) * TC + c] = op_sign(op, r) * v[op_perm(op, r)];
+        Ns[k * TC + c] = node;
+      }
+    }
+    __syncthreads();
+  } else {
+    // FP32 path: gather in FP64 into a scratch area that aliases nothing
+    // else (placed after Ns), take the per-cell mean, then round.
+    double *Ud = reinterpret_cast<double *>(
+        smem_raw + (((size_t)(m * m + m * TC) * sizeof(T) + (size_t)n * TC * 4 + 15) & ~(size_t)15));
+    double *mean = Ud + m * TC;
+    for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+      const int k = idx / TC, c = idx % TC;
+      if (c < nc) {
+        const int32_t node = cn[(int64_t)k * Cp + t.cell0 + c];
+        const int op = M.sym[gbase + c];
+        const double *un = u + 3 * (int64_t)node;
+        const double v[3] = {un[0], un[1], un[2]};
+#pragma unroll
+        for (int r = 0; r < 3; ++r) Ud[(3 * k + r) * TC + c] = op_sign(op, r) * v[op_perm(op, r)];
+        Ns[k * TC + c] = node;
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 3 * TC; idx += blockDim.x) {
+      const int r = idx / TC, c = idx % TC;
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += Ud[(3 * k + r) * TC + c];
+      mean[r * TC + c] = s / n;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
+      const int i = idx / TC, c = idx % TC;
+      Us[idx] = (T)(Ud[idx] - mean[(i % 3) * TC + c]);
+    }
+    __syncthreads();
+  }
+
+  const int c = threadIdx.x % TC;
+  const int G = blockDim.x / TC;
+  if (c < nc) {
+    const double s = M.scale[gbase + c];
+    const int op = M.sym[gbase + c];
+    for (int i = threadIdx.x / TC; i < m; i += G) {
+      T acc = 0;
+      const T *Kr = Ks + i * m;
+      for (int j = 0; j < m; ++j) acc = fma(Kr[j], Us[j * TC + c], acc);
+      const int k = i / 3, r = i - 3 * (i / 3);
+      atomicAdd(&f[3 * (int64_t)Ns[k * TC + c] + op_perm(op, r)], op_sign(op, r) * s * (double)acc);
+    }
+  }
+  if (blockIdx.x == 0) add_external(L, d_step, dt, f);
+}
+
+static size_t simt_smem(int m, bool fp32) {
+  const int n = m / 3, TC = SIMT_TILE;
+  size_t T = fp32 ? 4 : 8;
+  size_t b = (size_t)(m * m + m * TC) * T + (size_t)n * TC * 4;
+  if (fp32) b = ((b + 15) & ~(size_t)15) + (size_t)(m * TC + 3 * TC) * 8;
+  return b;
+}
+
+cudaError_t launch_force_simt(const sbx_ctx *ctx, const double *u, double *f, double dt,
+                              cudaStream_t s) {
+  const bool fp32 = ctx->prec == SBX_PREC_FP32;
+  const size_t smem = simt_smem(ctx->max_m, fp32);
+  if (ctx->n_tiles_simt == 0) return cudaSuccess;
+  if (fp32) {
+    auto k = k_force_simt<float, SIMT_TILE>;
+    k<<<ctx->n_tiles_simt, 256, smem, s>>>(ctx->d_tiles_simt, ctx->view(), ctx->d_K32, u, f,
+                                           ctx->loads(), ctx->d_step, dt);
+  } else {
+    auto k = k_force_simt<double, SIMT_TILE>;
+    k<<<ctx->n_tiles_simt, 256, smem, s>>>(ctx->d_tiles_simt, ctx->view(), ctx->d_K64, u, f,
+                                           ctx->loads(), ctx->d_step, dt);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_kernels() {
+  const int a = (int)simt_smem(78, false), b = (int)simt_smem(78, true);
+  cudaError_t e = cudaFuncSetAttribute(k_force_simt<double, SIMT_TILE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_force_simt<float, SIMT_TILE>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+}
+
+// ------------------------------------------------------------------ update
+// Eq. (DnMdiag) with f = R_int - R_ext:
+//   U_{n+1} = (-dt^2 M^-1 f + 2 U_n - (1 - a dt/2) U_{n-1}) / (1 + a dt/2),
+// written over U_{n-1}.  f is reset to zero for the next step (unless the
+// caller keeps it for read-back).  Thread 0 advances the device step index.
+__global__ void __launch_bounds__(256) k_update(int64_t nd, const double *__restrict__ minv,
+                                                double *__restrict__ f,
+                                                const double *__restrict__ uc,
+                                                double *__restrict__ up, double dt2, double cm,
+                                                double inv_cp, int zero_f, int32_t *flags,
+                                                int64_t *d_step) {
+  bool bad = false;
+  const int64_t n2 = nd / 2;
+  const double2 *f2 = reinterpret_cast<const double2 *>(f);
+  const double2 *m2 = reinterpret_cast<const double2 *>(minv);
+  const double2 *c2 = reinterpret_cast<const double2 *>(uc);
+  double2 *p2 = reinterpret_cast<double2 *>(up);
+  double2 *fz = reinterpret_cast<double2 *>(f);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 fv = f2[i], mv = m2[i], cv = c2[i], pv = p2[i];
+    double2 r;
+    r.x = (-dt2 * mv.x * fv.x + 2.0 * cv.x - cm * pv.x) * inv_cp;
+    r.y = (-dt2 * mv.y * fv.y + 2.0 * cv.y - cm * pv.y) * inv_cp;
+    bad |= !isfinite(r.x) || !isfinite(r.y);
+    p2[i] = r;
+    if (zero_f) fz[i] = make_double2(0.0, 0.0);
+  }
+  if ((nd & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t d = nd - 1;
+    const double r = (-dt2 * minv[d] * f[d] + 2.0 * uc[d] - cm * up[d]) * inv_cp;
+    bad |= !isfinite(r);
+    up[d] = r;
+    if (zero_f) f[d] = 0.0;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *d_step += 1;
+}
+
+static int update_grid(int64_t nd) {
+  int64_t want = (nd / 2 + 255) / 256;
+  int dev_sms = 152;
+  int64_t cap = (int64_t)dev_sms * 8;
+  return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+cudaError_t launch_update(const sbx_ctx *ctx, const double *uc, double *up, double *f, double dt,
+                          double alpha, int zero_f, cudaStream_t s) {
+  const int64_t nd = ctx->ndof * ctx->B;
+  const double cm = 1.0 - 0.5 * alpha * dt, cp = 1.0 + 0.5 * alpha * dt;
+  k_update<<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_minv, f, uc, up, dt * dt, cm, 1.0 / cp,
+                                           zero_f, ctx->d_flags, ctx->d_step);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- start-up
+// Eq. (D0): U_-1 = U_0 - dt V_0 + dt^2/2 A_0 with A_0 = -M^-1 f - alpha V_0,
+// f = K U_0 - R_ext(0).  Fixed DOFs (minv == 0) stay zero.
+__global__ void k_init_um1(int64_t nd, const double *minv, const double *u0, const double *v0,
+                           double *um1, const double *f, double dt, double alpha) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = v0 ? v0[i] : 0.0;
+    if (minv[i] == 0.0) {
+      um1[i] = 0.0;
+      continue;
+    }
+    const double acc = -minv[i] * f[i] - alpha * v;
+    um1[i] = u0[i] - dt * v + 0.5 * dt * dt * acc;
+  }
+}
+
+cudaError_t launch_init_um1(const sbx_ctx *ctx, const double *u0, const double *v0, double *um1,
+                            const double *f, double dt, double alpha, cudaStream_t s) {
+  const int64_t nd = ctx->ndof * ctx->B;
+  k_init_um1<<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_minv, u0, v0, um1, f, dt, alpha);
+  return cudaGetLastError();
+}
+
+__global__ void k_zero_fixed(int64_t nd, const double *minv, double *u) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (minv[i] == 0.0) u[i] = 0.0;
+}
+
+cudaError_t launch_zero_fixed(const sbx_ctx *ctx, double *u, cudaStream_t s) {
+  const int64_t nd = ctx->ndof * ctx->B;
+  k_zero_fixed<<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_minv, u);
+  return cudaGetLastError();
+}
+
+}  // namespace sbx

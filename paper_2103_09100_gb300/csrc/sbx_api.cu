@@ -1,0 +1,655 @@
+// C ABI of the explicit octree-SBFEM solver: context, validation, uploads,
+// step loop.  Declarations and argument contracts: include/sbx.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "sbx_internal.cuh"
+
+using sbx::Tile;
+
+namespace {
+
+int fail(sbx_ctx *ctx, int code, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(sbx_ctx *ctx, cudaError_t e, const char *where) {
+  return fail(ctx, SBX_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy `bytes` from a host or device pointer into host memory.
+int fetch(sbx_ctx *ctx, void *dst_host, const void *src, size_t bytes) {
+  if (bytes == 0) return SBX_OK;
+  if (!src) return fail(ctx, SBX_EINVAL, "null input array");
+  if (is_device_ptr(src)) {
+    CK(cudaMemcpyAsync(dst_host, src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else {
+    memcpy(dst_host, src, bytes);
+  }
+  return SBX_OK;
+}
+
+template <typename T>
+int fetch_vec(sbx_ctx *ctx, std::vector<T> &v, const T *src, size_t n) {
+  try {
+    v.resize(n);
+  } catch (const std::bad_alloc &) {
+    return fail(ctx, SBX_ENOMEM, "host allocation failed");
+  }
+  return fetch(ctx, v.data(), src, n * sizeof(T));
+}
+
+template <typename T>
+int dalloc(sbx_ctx *ctx, T **p, size_t n) {
+  if (*p) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(ctx, SBX_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return SBX_OK;
+}
+
+template <typename T>
+int upload(sbx_ctx *ctx, T **p, const std::vector<T> &v) {
+  int rc = dalloc(ctx, p, v.size());
+  if (rc) return rc;
+  if (!v.empty()) CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  return SBX_OK;
+}
+
+template <typename T>
+void dfree(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void drop_graph(sbx_ctx *ctx) {
+  for (auto &g : ctx->graph.exec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  ctx->graph.valid = false;
+}
+
+void free_mesh(sbx_ctx *ctx) {
+  drop_graph(ctx);
+  dfree(ctx->d_conn); dfree(ctx->d_conn_off); dfree(ctx->d_pat_cstart); dfree(ctx->d_pat_ccount);
+  dfree(ctx->d_sym); dfree(ctx->d_scale); dfree(ctx->d_minv); dfree(ctx->d_mass);
+  dfree(ctx->d_u[0]); dfree(ctx->d_u[1]); dfree(ctx->d_f); dfree(ctx->d_tiles_simt);
+  dfree(ctx->d_load_dof); dfree(ctx->d_load_amp); dfree(ctx->d_load_t1); dfree(ctx->d_load_ncyc);
+  dfree(ctx->d_load_kind);
+  ctx->n_load = 0;
+  ctx->have_mesh = false;
+}
+
+void free_patterns(sbx_ctx *ctx) {
+  dfree(ctx->d_K64); dfree(ctx->d_K32); dfree(ctx->d_pat_m); dfree(ctx->d_koff);
+  ctx->n_pat = 0;
+}
+
+int set_device(sbx_ctx *ctx) {
+  CK(cudaSetDevice(ctx->device));
+  return SBX_OK;
+}
+
+int force(sbx_ctx *ctx, const double *u, double *f, double dt) {
+  CK(sbx::launch_force_simt(ctx, u, f, dt, ctx->stream));
+  return SBX_OK;
+}
+
+// One CDM step from d_u[cur] (U_n) into d_u[cur ^ 1] (U_{n-1} -> U_{n+1}).
+int one_step(sbx_ctx *ctx, int parity, double dt, double alpha, int zero_f) {
+  double *uc = ctx->d_u[parity], *up = ctx->d_u[parity ^ 1];
+  int rc = force(ctx, uc, ctx->d_f, dt);
+  if (rc) return rc;
+  CK(sbx::launch_update(ctx, uc, up, ctx->d_f, dt, alpha, zero_f, ctx->stream));
+  return SBX_OK;
+}
+
+constexpr int GRAPH_UNIT = 32;  // steps per replayed graph (even)
+
+int build_graphs(sbx_ctx *ctx, double dt, double alpha) {
+  drop_graph(ctx);
+  for (int parity = 0; parity < 2; ++parity) {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = SBX_OK;
+    for (int s = 0; s < GRAPH_UNIT && rc == SBX_OK; ++s) rc = one_step(ctx, parity ^ (s & 1), dt, alpha, 1);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->graph.exec[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+  }
+  ctx->graph.valid = true;
+  ctx->graph.dt = dt;
+  ctx->graph.alpha = alpha;
+  ctx->graph.unit = GRAPH_UNIT;
+  return SBX_OK;
+}
+
+int check_flags(sbx_ctx *ctx) {
+  int32_t fl = 0;
+  CK(cudaMemcpyAsync(&fl, ctx->d_flags, sizeof(fl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (fl & 1) return fail(ctx, SBX_ENONFINITE, "non-finite value in the displacement field");
+  return SBX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbx_create(sbx_ctx **out, int device, void *cuda_stream) {
+  if (!out) return SBX_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return SBX_EINVAL;
+  }
+  sbx_ctx *ctx = new (std::nothrow) sbx_ctx();
+  if (!ctx) return SBX_ENOMEM;
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return SBX_ECUDA;
+  }
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return SBX_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  if (sbx::prepare_kernels() != cudaSuccess) {
+    cudaGetLastError();
+    sbx_destroy(ctx);
+    return SBX_ECUDA;
+  }
+  if (dalloc(ctx, &ctx->d_flags, 1) || dalloc(ctx, &ctx->d_step, 1)) {
+    sbx_destroy(ctx);
+    return SBX_ENOMEM;
+  }
+  cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t), ctx->stream);
+  cudaMemsetAsync(ctx->d_step, 0, sizeof(int64_t), ctx->stream);
+  *out = ctx;
+  return SBX_OK;
+}
+
+int sbx_destroy(sbx_ctx *ctx) {
+  if (!ctx) return SBX_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_mesh(ctx);
+  free_patterns(ctx);
+  dfree(ctx->d_flags);
+  dfree(ctx->d_step);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return SBX_OK;
+}
+
+const char *sbx_last_error(const sbx_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int sbx_sync(sbx_ctx *ctx) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return ctx->have_mesh ? check_flags(ctx) : SBX_OK;
+}
+
+int set_patterns(sbx_ctx *ctx, int n_patterns, const int32_t *n_nodes, const double *K_packed,
+                 const double *Mlump_packed) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (n_patterns < 1 || n_patterns > 144) return fail(ctx, SBX_EINVAL, "n_patterns must be in [1, 144]");
+  std::vector<int32_t> nn;
+  if (int rc = fetch_vec(ctx, nn, n_nodes, n_patterns)) return rc;
+  int64_t kt = 0, mt = 0;
+  for (int p = 0; p < n_patterns; ++p) {
+    if (nn[p] < 8 || nn[p] > 26) return fail(ctx, SBX_EINVAL, "pattern node count outside [8, 26]");
+    kt += 9LL * nn[p] * nn[p];
+    mt += 3LL * nn[p];
+  }
+  std::vector<double> K, Mv;
+  if (int rc = fetch_vec(ctx, K, K_packed, kt)) return rc;
+  if (int rc = fetch_vec(ctx, Mv, Mlump_packed, mt)) return rc;
+  std::vector<int64_t> koff(n_patterns), moff(n_patterns);
+  int64_t ko = 0, mo = 0;
+  for (int p = 0; p < n_patterns; ++p) {
+    const int m = 3 * nn[p];
+    koff[p] = ko;
+    moff[p] = mo;
+    double nrm = 0;
+    for (int i = 0; i < m * m; ++i) {
+      if (!isfinite(K[ko + i])) return fail(ctx, SBX_EINVAL, "non-finite entry in K_p");
+      nrm = fmax(nrm, fabs(K[ko + i]));
+    }
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < i; ++j)
+        if (fabs(K[ko + i * m + j] - K[ko + j * m + i]) > 1e-12 * nrm)
+          return fail(ctx, SBX_EINVAL, "K_p is not symmetric");
+    for (int i = 0; i < m; ++i)
+      if (!(Mv[mo + i] > 0) || !isfinite(Mv[mo + i])) return fail(ctx, SBX_EINVAL, "lumped mass must be positive");
+    ko += (int64_t)m * m;
+    mo += m;
+  }
+  free_mesh(ctx);
+  free_patterns(ctx);
+  std::vector<float> K32(K.begin(), K.end());
+  std::vector<int32_t> pm(n_patterns);
+  for (int p = 0; p < n_patterns; ++p) pm[p] = 3 * nn[p];
+  if (int rc = upload(ctx, &ctx->d_K64, K)) return rc;
+  if (int rc = upload(ctx, &ctx->d_K32, K32)) return rc;
+  if (int rc = upload(ctx, &ctx->d_pat_m, pm)) return rc;
+  if (int rc = upload(ctx, &ctx->d_koff, koff)) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->n_pat = n_patterns;
+  ctx->pat_nodes = nn;
+  ctx->pat_koff = koff;
+  ctx->pat_moff = moff;
+  ctx->K_host.swap(K);
+  ctx->M_host.swap(Mv);
+  return SBX_OK;
+}
+
+int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *cell_pattern,
+                const uint8_t *cell_sym, const int64_t *cell_ptr, const int32_t *cell_nodes,
+                const double *h, const double *E, const double *rho, int64_t n_fixed,
+                const int64_t *fixed_dofs, int n_rhs, int precision_mode) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (ctx->n_pat == 0) return fail(ctx, SBX_ESTATE, "set_patterns must come before mesh_upload");
+  if (n_nodes < 1 || n_cells < 1 || n_nodes > (int64_t)INT32_MAX)
+    return fail(ctx, SBX_EINVAL, "n_nodes / n_cells out of range");
+  if (n_rhs != 1) return fail(ctx, SBX_EINVAL, "n_rhs > 1 needs the batched build");
+  if (precision_mode != SBX_PREC_FP64 && precision_mode != SBX_PREC_FP32 &&
+      precision_mode != SBX_PREC_MIXED)
+    return fail(ctx, SBX_EINVAL, "unknown precision_mode");
+  std::vector<int32_t> pat;
+  std::vector<uint8_t> sym;
+  std::vector<int64_t> ptr, fixed;
+  std::vector<int32_t> nodes;
+  std::vector<double> hv, Ev, rv;
+  if (int rc = fetch_vec(ctx, pat, cell_pattern, n_cells)) return rc;
+  if (int rc = fetch_vec(ctx, sym, cell_sym, n_cells)) return rc;
+  if (int rc = fetch_vec(ctx, ptr, cell_ptr, n_cells + 1)) return rc;
+  if (ptr[0] != 0) return fail(ctx, SBX_EINVAL, "cell_ptr[0] must be 0");
+  for (int64_t e = 0; e < n_cells; ++e) {
+    if (pat[e] < 0 || pat[e] >= ctx->n_pat) return fail(ctx, SBX_EINVAL, "cell_pattern out of range");
+    if (sym[e] >= 48) return fail(ctx, SBX_EINVAL, "cell_sym must be < 48");
+    if (ptr[e + 1] - ptr[e] != ctx->pat_nodes[pat[e]])
+      return fail(ctx, SBX_EINVAL, "cell node count does not match its pattern");
+  }
+  if (int rc = fetch_vec(ctx, nodes, cell_nodes, ptr[n_cells])) return rc;
+  for (int64_t i = 0; i < ptr[n_cells]; ++i)
+    if (nodes[i] < 0 || nodes[i] >= n_nodes) return fail(ctx, SBX_EINVAL, "cell node id out of range");
+  if (int rc = fetch_vec(ctx, hv, h, n_cells)) return rc;
+  if (int rc = fetch_vec(ctx, Ev, E, n_cells)) return rc;
+  if (int rc = fetch_vec(ctx, rv, rho, n_cells)) return rc;
+  for (int64_t e = 0; e < n_cells; ++e)
+    if (!(hv[e] > 0) || !(Ev[e] > 0) || !(rv[e] > 0) || !isfinite(hv[e] * Ev[e] * rv[e]))
+      return fail(ctx, SBX_EINVAL, "h, E and rho must be positive and finite");
+  if (n_fixed < 0) return fail(ctx, SBX_EINVAL, "n_fixed < 0");
+  if (int rc = fetch_vec(ctx, fixed, fixed_dofs, n_fixed)) return rc;
+  const int64_t ndof = 3 * n_nodes;
+  for (int64_t i = 0; i < n_fixed; ++i)
+    if (fixed[i] < 0 || fixed[i] >= ndof) return fail(ctx, SBX_EINVAL, "fixed DOF out of range");
+
+  // group cells by pattern (stable: keeps the caller's order inside a group)
+  const int P = ctx->n_pat;
+  std::vector<int64_t> cnt(P, 0), start(P, 0);
+  for (int64_t e = 0; e < n_cells; ++e) cnt[pat[e]]++;
+  for (int p = 1; p < P; ++p) start[p] = start[p - 1] + cnt[p - 1];
+  std::vector<int64_t> order(n_cells), fillp(start);
+  for (int64_t e = 0; e < n_cells; ++e) order[fillp[pat[e]]++] = e;
+  std::vector<int64_t> conn_off(P, 0);
+  int64_t co = 0;
+  for (int p = 0; p < P; ++p) {
+    conn_off[p] = co;
+    co += cnt[p] * ctx->pat_nodes[p];
+  }
+  std::vector<int32_t> conn(std::max<int64_t>(co, 1));
+  std::vector<uint8_t> ssym(n_cells);
+  std::vector<double> scale(n_cells);
+  std::vector<double> mass(ndof, 0.0);
+  static const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  int max_m = 0;
+  for (int p = 0; p < P; ++p) {
+    const int np = ctx->pat_nodes[p];
+    if (cnt[p]) max_m = std::max(max_m, 3 * np);
+    for (int64_t j = 0; j < cnt[p]; ++j) {
+      const int64_t s = start[p] + j, e = order[s];
+      ssym[s] = sym[e];
+      scale[s] = Ev[e] * hv[e];
+      const double mscale = rv[e] * hv[e] * hv[e] * hv[e];
+      const int op = sym[e];
+      for (int k = 0; k < np; ++k) {
+        const int32_t node = nodes[ptr[e] + k];
+        conn[conn_off[p] + (int64_t)k * cnt[p] + j] = node;
+        // master component r of this node is cell component perm[r]
+        for (int r = 0; r < 3; ++r)
+          mass[3 * (int64_t)node + perm[op >> 3][r]] += mscale * ctx->M_host[ctx->pat_moff[p] + 3 * k + r];
+      }
+    }
+  }
+  std::vector<double> minv(ndof);
+  for (int64_t d = 0; d < ndof; ++d) {
+    if (!(mass[d] > 0)) return fail(ctx, SBX_EINVAL, "a node has no positive mass (unused node id?)");
+    minv[d] = 1.0 / mass[d];
+  }
+  for (int64_t i = 0; i < n_fixed; ++i) minv[fixed[i]] = 0.0;
+
+  std::vector<Tile> tiles;
+  for (int p = 0; p < P; ++p)
+    for (int64_t c0 = 0; c0 < cnt[p]; c0 += sbx::SIMT_TILE)
+      tiles.push_back(Tile{p, (int32_t)std::min<int64_t>(sbx::SIMT_TILE, cnt[p] - c0), c0});
+
+  free_mesh(ctx);
+  int rc = SBX_OK;
+  if (!rc) rc = upload(ctx, &ctx->d_conn, conn);
+  if (!rc) rc = upload(ctx, &ctx->d_conn_off, conn_off);
+  if (!rc) rc = upload(ctx, &ctx->d_pat_cstart, start);
+  if (!rc) rc = upload(ctx, &ctx->d_pat_ccount, cnt);
+  if (!rc) rc = upload(ctx, &ctx->d_sym, ssym);
+  if (!rc) rc = upload(ctx, &ctx->d_scale, scale);
+  if (!rc) rc = upload(ctx, &ctx->d_minv, minv);
+  if (!rc) rc = upload(ctx, &ctx->d_mass, mass);
+  if (!rc) rc = upload(ctx, &ctx->d_tiles_simt, tiles);
+  if (!rc) rc = dalloc(ctx, &ctx->d_u[0], ndof);
+  if (!rc) rc = dalloc(ctx, &ctx->d_u[1], ndof);
+  if (!rc) rc = dalloc(ctx, &ctx->d_f, ndof);
+  if (rc) {
+    free_mesh(ctx);
+    return rc;
+  }
+  CK(cudaMemsetAsync(ctx->d_u[0], 0, ndof * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_u[1], 0, ndof * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_f, 0, ndof * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(int64_t), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->N = n_nodes;
+  ctx->C = n_cells;
+  ctx->ndof = ndof;
+  ctx->B = n_rhs;
+  ctx->prec = precision_mode;
+  ctx->pat_cstart = start;
+  ctx->pat_ccount = cnt;
+  ctx->n_tiles_simt = (int)tiles.size();
+  ctx->max_m = max_m;
+  ctx->cur = 0;
+  ctx->step = 0;
+  ctx->f_dirty = false;
+  ctx->have_mesh = true;
+  return SBX_OK;
+}
+
+int set_load(sbx_ctx *ctx, int n_src, const int64_t *node, const double *dir3, const int32_t *rhs,
+             int wavelet, const double *t1, const double *P0, const double *ncyc) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before set_load");
+  if (n_src < 0) return fail(ctx, SBX_EINVAL, "n_src < 0");
+  if (wavelet < SBX_WAVE_RICKER || wavelet > SBX_WAVE_SINE_BURST) return fail(ctx, SBX_EINVAL, "unknown wavelet");
+  std::vector<int64_t> nd;
+  std::vector<double> dv, tv, pv, cv;
+  std::vector<int32_t> rv;
+  if (int rc = fetch_vec(ctx, nd, node, n_src)) return rc;
+  if (int rc = fetch_vec(ctx, dv, dir3, 3 * (size_t)n_src)) return rc;
+  if (int rc = fetch_vec(ctx, tv, t1, n_src)) return rc;
+  if (int rc = fetch_vec(ctx, pv, P0, n_src)) return rc;
+  if (ncyc) {
+    if (int rc = fetch_vec(ctx, cv, ncyc, n_src)) return rc;
+  } else {
+    cv.assign(n_src, 5.0);
+  }
+  if (rhs) {
+    if (int rc = fetch_vec(ctx, rv, rhs, n_src)) return rc;
+  } else {
+    rv.assign(n_src, 0);
+  }
+  std::vector<int64_t> ldof;
+  std::vector<double> lamp, lt1, lnc;
+  std::vector<int32_t> lkind;
+  for (int k = 0; k < n_src; ++k) {
+    if (nd[k] < 0 || nd[k] >= ctx->N) return fail(ctx, SBX_EINVAL, "load node out of range");
+    if (rv[k] < 0 || rv[k] >= ctx->B) return fail(ctx, SBX_EINVAL, "load rhs out of range");
+    if (!(tv[k] > 0)) return fail(ctx, SBX_EINVAL, "t1 must be positive");
+    for (int d = 0; d < 3; ++d) {
+      if (dv[3 * k + d] == 0.0) continue;
+      int64_t dof = 3 * nd[k] + d;
+      if (ctx->B > 1) dof = dof * ctx->B + rv[k];
+      ldof.push_back(dof);
+      lamp.push_back(pv[k] * dv[3 * k + d]);
+      lt1.push_back(tv[k]);
+      lnc.push_back(cv[k]);
+      lkind.push_back(wavelet);
+    }
+  }
+  drop_graph(ctx);
+  int rc = SBX_OK;
+  if (!rc) rc = upload(ctx, &ctx->d_load_dof, ldof);
+  if (!rc) rc = upload(ctx, &ctx->d_load_amp, lamp);
+  if (!rc) rc = upload(ctx, &ctx->d_load_t1, lt1);
+  if (!rc) rc = upload(ctx, &ctx->d_load_ncyc, lnc);
+  if (!rc) rc = upload(ctx, &ctx->d_load_kind, lkind);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->n_load = (int)ldof.size();
+  return SBX_OK;
+}
+
+int set_initial(sbx_ctx *ctx, const double *u0, const double *v0, double dt, double alpha) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before set_initial");
+  if (!(dt > 0) || !(alpha >= 0)) return fail(ctx, SBX_EINVAL, "dt must be > 0 and alpha >= 0");
+  const int64_t nd = ctx->ndof * ctx->B;
+  const size_t bytes = nd * sizeof(double);
+  ctx->cur = 0;
+  double *U0 = ctx->d_u[0], *Um1 = ctx->d_u[1];
+  if (u0) {
+    CK(cudaMemcpyAsync(U0, u0, bytes, cudaMemcpyDefault, ctx->stream));
+  } else {
+    CK(cudaMemsetAsync(U0, 0, bytes, ctx->stream));
+  }
+  CK(sbx::launch_zero_fixed(ctx, U0, ctx->stream));
+  double *V0 = nullptr;
+  if (v0) {
+    // staged through the (not yet used) force buffer's partner: U_-1 slot
+    CK(cudaMemcpyAsync(Um1, v0, bytes, cudaMemcpyDefault, ctx->stream));
+    CK(sbx::launch_zero_fixed(ctx, Um1, ctx->stream));
+    V0 = Um1;
+  }
+  CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(int64_t), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_f, 0, bytes, ctx->stream));
+  if (int rc = force(ctx, U0, ctx->d_f, dt)) return rc;
+  // k_init_um1 reads v0[i] before writing um1[i] of the same index
+  CK(sbx::launch_init_um1(ctx, U0, V0, Um1, ctx->d_f, dt, alpha, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_f, 0, bytes, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t), ctx->stream));
+  ctx->step = 0;
+  ctx->f_dirty = false;
+  return SBX_OK;
+}
+
+int step_n(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before step_n");
+  if (n_steps < 0 || !(dt > 0) || !(alpha >= 0) || !isfinite(dt) || !isfinite(alpha))
+    return fail(ctx, SBX_EINVAL, "need n_steps >= 0, dt > 0, alpha >= 0");
+  if (n_steps == 0) return SBX_OK;
+  const size_t bytes = ctx->ndof * ctx->B * sizeof(double);
+  if (ctx->f_dirty) {
+    CK(cudaMemsetAsync(ctx->d_f, 0, bytes, ctx->stream));
+    ctx->f_dirty = false;
+  }
+  int64_t left = n_steps - 1;  // the last step keeps R_int for read-back
+  if (left >= GRAPH_UNIT) {
+    if (!ctx->graph.valid || ctx->graph.dt != dt || ctx->graph.alpha != alpha)
+      if (int rc = build_graphs(ctx, dt, alpha)) return rc;
+    while (left >= GRAPH_UNIT) {
+      CK(cudaGraphLaunch(ctx->graph.exec[ctx->cur], ctx->stream));
+      left -= GRAPH_UNIT;
+    }
+  }
+  while (left > 0) {
+    if (int rc = one_step(ctx, ctx->cur, dt, alpha, 1)) return rc;
+    ctx->cur ^= 1;
+    --left;
+  }
+  if (int rc = one_step(ctx, ctx->cur, dt, alpha, 0)) return rc;
+  ctx->cur ^= 1;
+  ctx->f_dirty = true;
+  ctx->step += n_steps;
+  return SBX_OK;
+}
+
+int sbx_profile(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha, double *ms_force,
+                double *ms_update) {
+  if (!ctx || !ms_force || !ms_update) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before sbx_profile");
+  if (n_steps < 1 || !(dt > 0) || !(alpha >= 0)) return fail(ctx, SBX_EINVAL, "bad arguments");
+  const size_t bytes = ctx->ndof * ctx->B * sizeof(double);
+  if (ctx->f_dirty) {
+    CK(cudaMemsetAsync(ctx->d_f, 0, bytes, ctx->stream));
+    ctx->f_dirty = false;
+  }
+  std::vector<cudaEvent_t> ev(3 * n_steps, nullptr);
+  int rc = SBX_OK;
+  for (auto &e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) rc = SBX_ECUDA;
+  for (int64_t s = 0; s < n_steps && rc == SBX_OK; ++s) {
+    double *uc = ctx->d_u[ctx->cur], *up = ctx->d_u[ctx->cur ^ 1];
+    cudaEventRecord(ev[3 * s], ctx->stream);
+    rc = force(ctx, uc, ctx->d_f, dt);
+    cudaEventRecord(ev[3 * s + 1], ctx->stream);
+    if (rc == SBX_OK && sbx::launch_update(ctx, uc, up, ctx->d_f, dt, alpha, s + 1 < n_steps, ctx->stream) !=
+                            cudaSuccess)
+      rc = fail(ctx, SBX_ECUDA, "update launch failed");
+    cudaEventRecord(ev[3 * s + 2], ctx->stream);
+    ctx->cur ^= 1;
+    ctx->step += 1;
+  }
+  ctx->f_dirty = true;
+  double tf = 0, tu = 0;
+  if (rc == SBX_OK && cudaStreamSynchronize(ctx->stream) == cudaSuccess) {
+    for (int64_t s = 0; s < n_steps; ++s) {
+      float a = 0, b = 0;
+      cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
+      cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]);
+      tf += a;
+      tu += b;
+    }
+  } else if (rc == SBX_OK) {
+    rc = fail(ctx, SBX_ECUDA, "stream synchronisation failed");
+  }
+  for (auto &e : ev)
+    if (e) cudaEventDestroy(e);
+  *ms_force = tf;
+  *ms_update = tu;
+  if (rc) return rc;
+  return check_flags(ctx);
+}
+
+int sbx_get_step(sbx_ctx *ctx, int64_t *n_out) {
+  if (!ctx || !n_out) return SBX_EINVAL;
+  *n_out = ctx->step;
+  return SBX_OK;
+}
+
+int sbx_set_step(sbx_ctx *ctx, int64_t n) {
+  if (!ctx || n < 0) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->step = n;
+  CK(cudaMemcpyAsync(ctx->d_step, &ctx->step, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SBX_OK;
+}
+
+int read_field(sbx_ctx *ctx, int which, double *out, int64_t len) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
+  if (!out) return fail(ctx, SBX_EINVAL, "null output");
+  const double *src = nullptr;
+  int64_t need = ctx->ndof * ctx->B;
+  switch (which) {
+    case SBX_U_N: src = ctx->d_u[ctx->cur]; break;
+    case SBX_U_NM1: src = ctx->d_u[ctx->cur ^ 1]; break;
+    case SBX_F_INT: src = ctx->d_f; break;
+    case SBX_MASS: src = ctx->d_mass; need = ctx->ndof; break;
+    default: return fail(ctx, SBX_EINVAL, "unknown field");
+  }
+  if (len != need) return fail(ctx, SBX_EINVAL, "len does not match the field size");
+  CK(cudaMemcpyAsync(out, src, len * sizeof(double), cudaMemcpyDefault, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_flags(ctx);
+}
+
+int write_field(sbx_ctx *ctx, int which, const double *in, int64_t len) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
+  if (!in) return fail(ctx, SBX_EINVAL, "null input");
+  if (len != ctx->ndof * ctx->B) return fail(ctx, SBX_EINVAL, "len does not match the field size");
+  double *dst;
+  if (which == SBX_U_N)
+    dst = ctx->d_u[ctx->cur];
+  else if (which == SBX_U_NM1)
+    dst = ctx->d_u[ctx->cur ^ 1];
+  else
+    return fail(ctx, SBX_EINVAL, "only U_N and U_NM1 can be written");
+  CK(cudaMemcpyAsync(dst, in, len * sizeof(double), cudaMemcpyDefault, ctx->stream));
+  return SBX_OK;
+}
+
+}  // extern "C"

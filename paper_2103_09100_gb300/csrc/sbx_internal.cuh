@@ -1,0 +1,123 @@
+// Internal declarations of the sbx library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sbx.h"
+
+namespace sbx {
+
+// A tile: up to `ncell` consecutive cells of one pattern.  `cell0` is the
+// index of the first cell inside its pattern group.
+struct Tile {
+  int32_t pat;
+  int32_t ncell;
+  int64_t cell0;
+};
+
+// Time function of the point loads (Sec. 5): kind, t1, peak, cycles.
+struct LoadTable {
+  int n;                 // number of (dof, load) entries
+  const int64_t *dof;    // DOF index (batched: (3 node + d) * B + b)
+  const double *amp;     // P0 * dir component
+  const int32_t *kind;   // SBX_WAVE_*
+  const double *t1;
+  const double *ncyc;
+};
+
+// Everything a force kernel needs about the mesh; device pointers.
+struct MeshView {
+  int64_t n_dof;              // 3 N (per load case)
+  int B;                      // load cases
+  const int32_t *pat_m;       // m_p = 3 n_p
+  const int64_t *koff;        // offset of K_p in the packed pattern arrays
+  const int32_t *conn;        // per pattern: [n_p][C_p] node ids (slot-major)
+  const int64_t *conn_off;    // offset of pattern p's block in conn
+  const int64_t *pat_cstart;  // first sorted cell of pattern p
+  const int64_t *pat_ccount;  // C_p
+  const uint8_t *sym;         // op per sorted cell
+  const double *scale;        // s_e = E_e h_e per sorted cell
+};
+
+struct GraphCache {
+  bool valid = false;
+  double dt = 0, alpha = 0;
+  int unit = 0;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+};
+
+}  // namespace sbx
+
+struct sbx_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+
+  // patterns
+  int n_pat = 0;
+  std::vector<int32_t> pat_nodes;
+  std::vector<int64_t> pat_koff;   // offsets in the packed K (m_p^2 each)
+  std::vector<int64_t> pat_moff;   // offsets in the packed lumped mass
+  std::vector<double> K_host, M_host;
+  double *d_K64 = nullptr;         // packed K_p, FP64
+  float *d_K32 = nullptr;          // packed K_p rounded to FP32
+  int32_t *d_pat_m = nullptr;
+  int64_t *d_koff = nullptr;
+
+  // mesh
+  bool have_mesh = false;
+  int64_t N = 0, C = 0, ndof = 0;  // ndof = 3 N (one load case)
+  int B = 1, prec = SBX_PREC_FP64;
+  std::vector<int64_t> pat_cstart, pat_ccount;
+  int32_t *d_conn = nullptr;
+  int64_t *d_conn_off = nullptr, *d_pat_cstart = nullptr, *d_pat_ccount = nullptr;
+  uint8_t *d_sym = nullptr;
+  double *d_scale = nullptr;
+  double *d_minv = nullptr;        // 1 / M_diag, 0 on fixed DOFs ([3N])
+  double *d_mass = nullptr;        // M_diag ([3N])
+  double *d_u[2] = {nullptr, nullptr};
+  int cur = 0;                     // d_u[cur] = U_n, d_u[cur ^ 1] = U_{n-1}
+  double *d_f = nullptr;           // R_int - R_ext accumulator
+  bool f_dirty = false;
+  int32_t *d_flags = nullptr;
+  int64_t *d_step = nullptr;       // device copy of the step index
+  int64_t step = 0;
+  sbx::Tile *d_tiles_simt = nullptr;
+  int n_tiles_simt = 0;
+  int max_m = 0;
+
+  // loads
+  int n_load = 0;
+  int64_t *d_load_dof = nullptr;
+  double *d_load_amp = nullptr, *d_load_t1 = nullptr, *d_load_ncyc = nullptr;
+  int32_t *d_load_kind = nullptr;
+
+  sbx::GraphCache graph;
+
+  sbx::MeshView view() const {
+    return sbx::MeshView{ndof, B, d_pat_m, d_koff, d_conn, d_conn_off, d_pat_cstart,
+                         d_pat_ccount, d_sym, d_scale};
+  }
+  sbx::LoadTable loads() const {
+    return sbx::LoadTable{n_load, d_load_dof, d_load_amp, d_load_kind, d_load_t1, d_load_ncyc};
+  }
+};
+
+namespace sbx {
+// kernels_simt.cu
+constexpr int SIMT_TILE = 32;
+cudaError_t launch_force_simt(const sbx_ctx *ctx, const double *u, double *f, double dt,
+                              cudaStream_t s);
+cudaError_t launch_update(const sbx_ctx *ctx, const double *uc, double *up, double *f, double dt,
+                          double alpha, int zero_f, cudaStream_t s);
+cudaError_t launch_init_um1(const sbx_ctx *ctx, const double *u0, const double *v0, double *um1,
+                            const double *f, double dt, double alpha, cudaStream_t s);
+cudaError_t launch_zero_fixed(const sbx_ctx *ctx, double *u, cudaStream_t s);
+// Opt every kernel into the shared-memory size it may need (call once per
+// device, outside stream capture).
+cudaError_t prepare_kernels();
+}  // namespace sbx

@@ -1,0 +1,101 @@
+"""High-level set-up of the GPU explicit solver (Algorithm 1 lines 1-7).
+
+``Solver`` takes a balanced octree mesh as plain arrays (26 node slots per
+cell, 12-bit hanging-node mask, edge length, modulus, density, fixed nodes,
+point loads), classifies the cells into master patterns, computes the
+pattern matrices, picks the time step from the element critical step
+(Eqs. tcr, tcr_scale) and hands everything to the C library.  Every time
+step then runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib as L
+from . import patterns
+
+PRECISIONS = {"fp64": L.SBX_PREC_FP64, "mixed": L.SBX_PREC_MIXED, "fp32": L.SBX_PREC_FP32}
+WAVES = {"ricker": L.SBX_WAVE_RICKER, "triangle": L.SBX_WAVE_TRIANGLE,
+         "sine_burst": L.SBX_WAVE_SINE_BURST}
+
+
+class Solver:
+    def __init__(self, slot_node, mask, h, E, rho, nu, n_nodes, fixed_nodes=(), sources=(),
+                 precision="fp64", n_rhs=1, device=0, stream=None, dt=None, dt_factor=0.5,
+                 alpha=0.0):
+        self.n_nodes = int(n_nodes)
+        self.n_rhs = int(n_rhs)
+        self.precision = precision
+        masters, cell_pattern, cell_sym, cell_ptr, cell_nodes = patterns.classify_mesh(
+            np.asarray(slot_node), np.asarray(mask))
+        nn, K, Ml, dts = patterns.pattern_arrays(masters, nu)
+        h = np.ascontiguousarray(h, np.float64)
+        E = np.ascontiguousarray(E, np.float64)
+        rho = np.ascontiguousarray(rho, np.float64)
+        self.dt_cr = float(np.min(np.sqrt(rho / E) * h * dts[cell_pattern]))
+        self.dt = float(dt) if dt is not None else dt_factor * self.dt_cr
+        self.alpha = float(alpha)
+        self.masters = masters
+        self.pattern_counts = np.bincount(cell_pattern, minlength=len(masters))
+        fixed_nodes = np.asarray(fixed_nodes, np.int64)
+        fixed = np.sort(np.concatenate([3 * fixed_nodes + d for d in range(3)])).astype(np.int64)
+        self.ctx = L.sbx_create(device, stream)
+        try:
+            L.set_patterns(self.ctx, nn, K, Ml)
+            L.mesh_upload(self.ctx, self.n_nodes, cell_pattern, cell_sym, cell_ptr, cell_nodes,
+                          h, E, rho, np.ascontiguousarray(fixed), self.n_rhs, PRECISIONS[precision])
+            if len(sources):
+                self.set_sources(sources)
+        except Exception:
+            L.sbx_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    @classmethod
+    def from_mesh(cls, mesh, **kw):
+        return cls(mesh.slot_node, mesh.mask, mesh.h, mesh.E, mesh.rho, mesh.nu, mesh.n_nodes,
+                   fixed_nodes=mesh.fixed_nodes, sources=mesh.sources, **kw)
+
+    def set_sources(self, sources):
+        kinds = {s["wavelet"] for s in sources}
+        if len(kinds) != 1:
+            raise ValueError("one wavelet kind per set_load call")
+        node = np.array([s["node"] for s in sources], np.int64)
+        d = np.ascontiguousarray(np.array([s["dir"] for s in sources], np.float64).ravel())
+        rhs = np.array([s.get("rhs", 0) for s in sources], np.int32)
+        t1 = np.array([s["t1"] for s in sources], np.float64)
+        P0 = np.array([s["P0"] for s in sources], np.float64)
+        nc = np.array([s.get("n_cycles", 5.0) for s in sources], np.float64)
+        L.set_load(self.ctx, node, d, rhs, WAVES[kinds.pop()], t1, P0, nc)
+
+    @property
+    def n_dof(self):
+        return 3 * self.n_nodes
+
+    def initial(self, u0=None, v0=None):
+        L.set_initial(self.ctx, u0, v0, self.dt, self.alpha)
+
+    def step(self, n):
+        L.step_n(self.ctx, n, self.dt, self.alpha)
+
+    def field(self, which=L.SBX_U_N, out=None):
+        n = self.n_dof * (1 if which == L.SBX_MASS else self.n_rhs)
+        out = np.empty(n) if out is None else out
+        return L.read_field(self.ctx, which, out)
+
+    def write(self, which, values):
+        L.write_field(self.ctx, which, np.ascontiguousarray(values, np.float64))
+
+    def sync(self):
+        L.sbx_sync(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            L.sbx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,266 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Metric (relative error, reading of the paper's accuracy discussion):
+rel = ||u_gpu - u_ref||_2 / ||u_ref||_2, checked at every 100th step and at
+the end.  FP64 bar: 1e-12.  FP32-contraction bar: 1e-5.
+"""
+import numpy as np
+import pytest
+
+import octree_gen as og
+from oracle import cdm, cube, sbfem
+from paper_2103_09100_gb300 import Solver, _lib as L, build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    L.load()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _solver(mesh, P, precision="fp64", alpha=0.0):
+    return Solver.from_mesh(mesh, precision=precision, dt=P.dt, alpha=alpha)
+
+
+def _tiny(seed=0, p=0.35):
+    m = og.tiny_refined(seed, p=p)
+    rng = np.random.default_rng(seed)
+    m.E = np.exp(0.3 * rng.standard_normal(m.n_cells))
+    m.fixed_nodes = np.where(np.abs(m.node_xyz[:, 2]) < 1e-12)[0]
+    top = og.nearest_node(m, (0.5, 0.5, 1.0))
+    m.sources = [og.point_source(top, (0.2, -0.1, -1), og.ricker_t1_for_mesh(m, 4.0))]
+    return m
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_single_force_tiny(seed):
+    m = _tiny(seed)
+    P = cdm.make_problem(m)
+    u0 = np.random.default_rng(seed).standard_normal(m.n_dof)
+    u0[P.fixed] = 0
+    S = _solver(m, P)
+    S.initial(u0)
+    S.step(1)
+    f_gpu = S.field(L.SBX_F_INT)
+    f_ref = cdm.apply_K(P, u0) - cdm.external_force(P, 0)
+    assert rel(f_gpu, f_ref) < 1e-13
+    # U_1 and U_0
+    u0r, um1r = cdm.initial_state(P, u0)
+    u1r, _, _, _ = cdm.run(P, 1, u0r, um1r)
+    assert rel(S.field(L.SBX_U_N), u1r) < 1e-13
+    assert rel(S.field(L.SBX_U_NM1), u0r) < 1e-15
+
+
+def test_mass_matches_oracle():
+    m = og.config_corner_cube()
+    P = cdm.make_problem(m)
+    S = _solver(m, P)
+    assert rel(S.field(L.SBX_MASS), P.M_diag) < 1e-14
+
+
+def _run_pair(m, P, S, n_total, chunk=100):
+    u, up = cdm.initial_state(P)
+    S.initial()
+    worst = 0.0
+    done = 0
+    while done < n_total:
+        k = min(chunk, n_total - done)
+        u, up, _, _ = cdm.run(P, k, u, up, n0=done, threads=4)
+        S.step(k)
+        done += k
+        worst = max(worst, rel(S.field(L.SBX_U_N), u))
+    return worst, rel(S.field(L.SBX_U_NM1), up)
+
+
+def test_corner_cube_1000_steps_fp64():
+    m = og.config_corner_cube()
+    P = cdm.make_problem(m)
+    S = _solver(m, P)
+    worst, last_prev = _run_pair(m, P, S, 1000)
+    print("corner cube FP64 max rel error over 1000 steps: %.3e" % worst)
+    assert worst < 1e-12 and last_prev < 1e-12
+
+
+def test_corner_cube_damped_fp64():
+    m = og.config_corner_cube()
+    P = cdm.make_problem(m, alpha=0.3)
+    S = _solver(m, P, alpha=0.3)
+    worst, _ = _run_pair(m, P, S, 300, chunk=75)
+    assert worst < 1e-12
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 65, 97])
+def test_step_counts_and_graph_replay(n):
+    m = _tiny(1)
+    P = cdm.make_problem(m)
+    u, up = cdm.initial_state(P)
+    S = _solver(m, P)
+    S.initial()
+    S.step(n)
+    if n:
+        u, up, _, _ = cdm.run(P, n, u, up)
+    assert L.sbx_get_step(S.ctx) == n
+    ref = np.linalg.norm(u) or 1.0
+    assert np.linalg.norm(S.field(L.SBX_U_N) - u) <= 1e-12 * ref + 1e-300
+
+
+def test_resume_from_written_state():
+    m = _tiny(2)
+    P = cdm.make_problem(m)
+    S = _solver(m, P)
+    S.initial()
+    S.step(70)
+    un, unm1 = S.field(L.SBX_U_N), S.field(L.SBX_U_NM1)
+    S.step(50)
+    cont = S.field(L.SBX_U_N)
+    R = _solver(m, P)
+    R.write(L.SBX_U_N, un)
+    R.write(L.SBX_U_NM1, unm1)
+    L.sbx_set_step(R.ctx, 70)
+    R.step(50)
+    assert rel(R.field(L.SBX_U_N), cont) < 1e-13
+
+
+def test_oracle_patterns_through_the_abi():
+    # the kernels fed the ORACLE's master matrices and transforms (its own
+    # canonical masks and ops follow the same op convention) reproduce the
+    # oracle's force: kernel parity independent of the product's set-up
+    m = _tiny(0)
+    P = cdm.make_problem(m)
+    canon_tab, op_tab = cube.canonical_table()
+    pats = P.tables["patterns"]
+    pidx = {p: i for i, p in enumerate(pats)}
+    nn = np.array([len(cube.present_slots(p)) for p in pats], np.int32)
+    K = np.concatenate([sbfem.master_cell(p).K.ravel() for p in pats])
+    Ml = np.concatenate([sbfem.master_cell(p).M_lump for p in pats])
+    cp, cs, ptr, nodes = [], [], [0], []
+    for c in range(m.n_cells):
+        mask = int(m.mask[c])
+        canon, op = int(canon_tab[mask]), int(op_tab[mask])
+        pi = cube.slot_perm(op)
+        inv = {pi[s]: s for s in range(26)}
+        cp.append(pidx[canon]); cs.append(op)
+        nd = [m.slot_node[c, inv[t]] for t in cube.present_slots(canon)]
+        nodes += nd
+        ptr.append(ptr[-1] + len(nd))
+    ctx = L.sbx_create(0)
+    try:
+        L.set_patterns(ctx, nn, K, Ml)
+        L.mesh_upload(ctx, m.n_nodes, np.array(cp, np.int32), np.array(cs, np.uint8),
+                      np.array(ptr, np.int64), np.array(nodes, np.int32), m.h, m.E, m.rho,
+                      P.fixed.astype(np.int64))
+        u0 = np.random.default_rng(9).standard_normal(m.n_dof)
+        u0[P.fixed] = 0
+        L.set_initial(ctx, u0, None, P.dt)
+        L.step_n(ctx, 1, P.dt)
+        f = np.empty(m.n_dof)
+        L.read_field(ctx, L.SBX_F_INT, f)
+        assert rel(f, cdm.apply_K(P, u0)) < 1e-13
+    finally:
+        L.sbx_destroy(ctx)
+
+
+def test_fp32_contraction_corner_cube():
+    m = og.config_corner_cube()
+    P = cdm.make_problem(m)
+    S = _solver(m, P, precision="fp32")
+    worst, _ = _run_pair(m, P, S, 1000)
+    print("corner cube FP32-contraction max rel error over 1000 steps: %.3e" % worst)
+    assert worst < 1e-5
+
+
+def test_nonfinite_flag_above_critical_step():
+    m = _tiny(0)
+    P = cdm.make_problem(m)
+    S = Solver.from_mesh(m, dt=8.0 * P.dt)
+    S.initial(np.random.default_rng(0).standard_normal(m.n_dof))
+    S.step(4000)
+    with pytest.raises(L.SbxError) as e:
+        S.field(L.SBX_U_N)
+    assert e.value.code == L.SBX_ENONFINITE
+
+
+def test_invalid_inputs_are_rejected():
+    m = _tiny(0)
+    ctx = L.sbx_create(0)
+    try:
+        with pytest.raises(L.SbxError) as e:
+            L.step_n(ctx, 1, 0.1)
+        assert e.value.code == L.SBX_ESTATE
+        K = np.eye(24).ravel() * 1.0
+        K[1] = 0.5     # not symmetric
+        with pytest.raises(L.SbxError) as e:
+            L.set_patterns(ctx, np.array([8], np.int32), K, np.ones(24))
+        assert e.value.code == L.SBX_EINVAL
+        L.set_patterns(ctx, np.array([8], np.int32), np.eye(24).ravel().copy(), np.ones(24))
+        bad = np.array([0, 1, 2, 3, 4, 5, 6, 99], np.int32)
+        with pytest.raises(L.SbxError) as e:
+            L.mesh_upload(ctx, 8, np.zeros(1, np.int32), np.zeros(1, np.uint8),
+                          np.array([0, 8], np.int64), bad, np.ones(1), np.ones(1), np.ones(1),
+                          np.zeros(0, np.int64))
+        assert e.value.code == L.SBX_EINVAL
+        with pytest.raises(L.SbxError) as e:
+            L.mesh_upload(ctx, 8, np.zeros(1, np.int32), np.full(1, 48, np.uint8),
+                          np.array([0, 8], np.int64), np.arange(8, dtype=np.int32), np.ones(1),
+                          np.ones(1), np.ones(1), np.zeros(0, np.int64))
+        assert e.value.code == L.SBX_EINVAL
+    finally:
+        L.sbx_destroy(ctx)
+
+
+def test_single_cell_mesh_and_no_loads():
+    m = og.small_uniform(1)
+    P = cdm.make_problem(m, sources=[])
+    m.sources = []
+    S = _solver(m, P)
+    u0 = np.random.default_rng(4).standard_normal(m.n_dof)
+    S.initial(u0)
+    S.step(40)
+    u, up = cdm.initial_state(P, u0)
+    u, _, _, _ = cdm.run(P, 40, u, up)
+    assert rel(S.field(L.SBX_U_N), u) < 1e-12
+
+
+@pytest.fixture(scope="module")
+def cavity():
+    m = og.config_cavity_cube()
+    P = cdm.make_problem(m)
+    return m, P
+
+
+def test_full_size_cavity_force(cavity):
+    # one internal-force evaluation on the full ~1M-cell mesh, in the same
+    # launch configuration the benchmark times
+    m, P = cavity
+    S = _solver(m, P)
+    u0 = np.random.default_rng(1).standard_normal(m.n_dof)
+    u0[P.fixed] = 0
+    S.initial(u0)
+    S.step(1)
+    f = S.field(L.SBX_F_INT)
+    ref = cdm.apply_K(P, u0) - cdm.external_force(P, 0)
+    assert rel(f, ref) < 1e-13
+    idx = np.random.default_rng(2).choice(m.n_dof, 2000, replace=False)
+    assert np.abs(f[idx] - ref[idx]).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_full_size_cavity_20_steps(cavity):
+    m, P = cavity
+    for prec, tol in [("fp64", 1e-12), ("fp32", 1e-6)]:
+        S = _solver(m, P, precision=prec)
+        u, up = cdm.initial_state(P)
+        u0 = np.random.default_rng(3).standard_normal(m.n_dof) * 1e-3
+        u0[P.fixed] = 0
+        u, up = cdm.initial_state(P, u0)
+        S.initial(u0)
+        S.step(20)
+        u, up, _, _ = cdm.run(P, 20, u, up, threads=8)
+        e = rel(S.field(L.SBX_U_N), u)
+        print("cavity %s 20-step rel error %.3e" % (prec, e))
+        assert e < tol
