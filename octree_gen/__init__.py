@@ -333,15 +333,17 @@ def config_corner_cube(seed=0, lmin=2, lmax=4, r0=0.65, p=0.15):
     return m
 
 
-def config_cavity_cube(seed=1, lmin=4, lmax=8, radius=0.2, band=0.075, sigma=0.3):
+def config_cavity_cube(seed=1, lmin=4, lmax=8, radius=0.2, band=0.072, sigma=0.3, p=0.002):
     """Cube minus a ball of radius 0.2 at the centre (staircase), levels 4-8
-    refined in a band around the sphere, E_e lognormal(sigma) per cell
-    (~1M cells at the default band), z = 0 fixed, Ricker at the top centre."""
+    refined in a band around the sphere plus seeded random flags with
+    probability p per cell and level, E_e lognormal(sigma) per cell
+    (~1M cells at the defaults), z = 0 fixed, Ricker at the top centre."""
     ctr = np.array([0.5, 0.5, 0.5])
+    frng = np.random.default_rng(seed + 1000)
 
     def refine(q, c, hq):
         d = np.linalg.norm(c - ctr[None, :], axis=1)
-        return np.abs(d - radius) < band + 0.9 * hq
+        return (np.abs(d - radius) < band + 0.9 * hq) | (frng.random(len(c)) < p)
 
     def remove(c):
         return np.linalg.norm(c - ctr[None, :], axis=1) < radius
