@@ -200,6 +200,49 @@ int write_field(sbx_ctx *ctx, int which, const double *in, int64_t len);
 int sbx_profile(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha,
                 double *ms_force, double *ms_update);
 
+/*
+ * sbx_step_static: one undamped explicit step with no external load that
+ * allocates nothing.  The paper has no counterpart; this entry point exists
+ * for callers that cannot allocate device memory: code that runs while a
+ * framework's caching allocator owns the whole device, real-time or
+ * embedded loops where cudaMalloc (which may synchronise the device or fail
+ * under memory pressure) is not allowed, and plug-ins that may only touch
+ * the buffers they are handed.  It computes
+ *   f = sum_e E_e h_e T_e^T K_p T_e u_e          (same kernel arithmetic as step_n)
+ *   U_{n+1} = -dt^2 minv f + 2 U_n - U_{n-1}     written over u_nm1
+ * in FP64 on the CURRENT device and enqueues the work on cuda_stream
+ * (NULL = legacy default stream); it neither synchronises nor allocates.
+ *
+ *   n_dof          3 N, at most SBX_STATIC_MAX_DOF (larger sizes: SBX_EINVAL).
+ *   n_patterns     P, 1 .. SBX_STATIC_MAX_PATTERNS.
+ *   pat_nodes[P], pat_cells[P]   HOST arrays: nodes of each master and the
+ *                  number of cells of each pattern; cells are stored grouped
+ *                  by pattern in pattern order.
+ *   K_packed       DEVICE, the P master stiffnesses as in set_patterns.
+ *   conn           DEVICE, per pattern p a block [n_p][C_p] of node ids in
+ *                  master node order (slot-major), blocks in pattern order.
+ *   sym[C], scale[C]  DEVICE, op (as in mesh_upload) and E_e h_e per cell.
+ *   minv[n_dof]    DEVICE, 1 / M_diag with 0 on fixed DOFs.
+ *   u_n[n_dof]     DEVICE, U_n (read).  u_nm1[n_dof]: DEVICE, U_{n-1} on
+ *                  entry, U_{n+1} on return of the enqueued work.
+ * Working memory: one library-owned static device array of
+ * SBX_STATIC_MAX_DOF doubles (32 MiB) that every GPU loading the library
+ * holds until exit.  All calls share it and it keeps the last call's
+ * contents (each call clears the part it uses first), so calls whose work
+ * overlaps on the GPU (different streams, or different host threads on one
+ * device) race and must be ordered by the caller.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * must come before any stream capture.
+ *   Errors: SBX_EINVAL (sizes, NULL pointers, dt <= 0), SBX_ECUDA.
+ */
+#define SBX_STATIC_MAX_DOF      (4 * 1024 * 1024)
+#define SBX_STATIC_MAX_PATTERNS 144
+int sbx_step_static(void *cuda_stream, int64_t n_dof, int n_patterns,
+                    const int32_t *pat_nodes, const int64_t *pat_cells,
+                    const double *K_packed, const int32_t *conn, const uint8_t *sym,
+                    const double *scale, const double *minv, double dt,
+                    const double *u_n, double *u_nm1);
+
 #ifdef __cplusplus
 }
 #endif

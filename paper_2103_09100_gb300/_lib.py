@@ -25,7 +25,9 @@ STATUS_NAMES = {0: "SBX_OK", 1: "SBX_EINVAL", 2: "SBX_ENOMEM", 3: "SBX_ECUDA",
 # every symbol include/sbx.h declares
 EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patterns",
            "mesh_upload", "set_load", "set_initial", "step_n", "sbx_get_step", "sbx_set_step",
-           "read_field", "write_field", "sbx_profile"]
+           "read_field", "write_field", "sbx_profile", "sbx_step_static"]
+SBX_STATIC_MAX_DOF = 4 * 1024 * 1024
+SBX_STATIC_MAX_PATTERNS = 144
 
 
 class SbxError(RuntimeError):
@@ -60,6 +62,7 @@ def load(path: str = LIB_PATH):
         "read_field": [vp, i32, vp, i64],
         "write_field": [vp, i32, vp, i64],
         "sbx_profile": [vp, i64, dbl, dbl, C.POINTER(dbl), C.POINTER(dbl)],
+        "sbx_step_static": [vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, dbl, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -163,6 +166,18 @@ def sbx_profile(ctx, n_steps, dt, alpha=0.0):
     a, b = C.c_double(), C.c_double()
     _check(ctx, load().sbx_profile(ctx, int(n_steps), float(dt), float(alpha), C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def sbx_step_static(stream, n_dof, pat_nodes, pat_cells, K_packed, conn, sym, scale, minv, dt,
+                    u_n, u_nm1):
+    """One step that allocates nothing (device arrays in, u_nm1 overwritten
+    with U_{n+1}); pat_nodes / pat_cells are host arrays."""
+    rc = load().sbx_step_static(C.c_void_p(stream) if stream else None, int(n_dof),
+                                len(pat_nodes), _ptr(pat_nodes, np.int32), _ptr(pat_cells, np.int64),
+                                _ptr(K_packed), _ptr(conn), _ptr(sym), _ptr(scale), _ptr(minv),
+                                float(dt), _ptr(u_n), _ptr(u_nm1))
+    if rc != SBX_OK:
+        raise SbxError(rc, "sbx_step_static failed")
 
 
 def write_field(ctx, which, src):
