@@ -111,6 +111,11 @@ void free_mesh(sbx_ctx *ctx) {
   dfree(ctx->d_u[0]); dfree(ctx->d_u[1]); dfree(ctx->d_f); dfree(ctx->d_tiles_simt);
   dfree(ctx->d_load_dof); dfree(ctx->d_load_amp); dfree(ctx->d_load_t1); dfree(ctx->d_load_ncyc);
   dfree(ctx->d_load_kind);
+  dfree(ctx->d_tc_pat); dfree(ctx->d_tc_K); dfree(ctx->d_tc_lidx); dfree(ctx->d_tc_nodes);
+  for (int c = 0; c < sbx::TC_CLASSES; ++c) {
+    dfree(ctx->d_tc_tiles[c]);
+    ctx->n_tc_tiles[c] = 0;
+  }
   ctx->n_load = 0;
   ctx->have_mesh = false;
 }
@@ -126,7 +131,11 @@ int set_device(sbx_ctx *ctx) {
 }
 
 int force(sbx_ctx *ctx, const double *u, double *f, double dt) {
-  CK(sbx::launch_force_simt(ctx, u, f, dt, ctx->stream));
+  if (ctx->prec == SBX_PREC_MIXED) {
+    CK(sbx::launch_force_tc(ctx, u, f, dt, ctx->stream));
+  } else {
+    CK(sbx::launch_force_simt(ctx, u, f, dt, ctx->stream));
+  }
   return SBX_OK;
 }
 
@@ -166,6 +175,7 @@ int check_flags(sbx_ctx *ctx) {
   int32_t fl = 0;
   CK(cudaMemcpyAsync(&fl, ctx->d_flags, sizeof(fl), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  if (fl & 2) return fail(ctx, SBX_ETIMEOUT, "a tensor-core completion wait gave up");
   if (fl & 1) return fail(ctx, SBX_ENONFINITE, "non-finite value in the displacement field");
   return SBX_OK;
 }
@@ -198,7 +208,7 @@ int sbx_create(sbx_ctx **out, int device, void *cuda_stream) {
     }
     ctx->own_stream = true;
   }
-  if (sbx::prepare_kernels() != cudaSuccess) {
+  if (sbx::prepare_kernels() != cudaSuccess || sbx::prepare_tc_kernels() != cudaSuccess) {
     cudaGetLastError();
     sbx_destroy(ctx);
     return SBX_ECUDA;
@@ -401,6 +411,14 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   if (rc) {
     free_mesh(ctx);
     return rc;
+  }
+  if (precision_mode == SBX_PREC_MIXED) {
+    std::string e;
+    const int trc = sbx::tc_setup(ctx, conn, conn_off, cnt, start, e);
+    if (trc) {
+      free_mesh(ctx);
+      return fail(ctx, trc, e);
+    }
   }
   CK(cudaMemsetAsync(ctx->d_u[0], 0, ndof * sizeof(double), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_u[1], 0, ndof * sizeof(double), ctx->stream));

@@ -42,6 +42,25 @@ struct MeshView {
   const double *scale;        // s_e = E_e h_e per sorted cell
 };
 
+constexpr int TC_CLASSES = 3;
+
+// Tensor-core path: a tile of up to 128 cells of one pattern and its unique
+// nodes (tile_nodes[node_off .. node_off + n_nodes)).
+struct TcTile {
+  int32_t pat;
+  int32_t ncell;
+  int64_t cell0;      // first cell inside the pattern group
+  int64_t node_off;
+  int32_t n_nodes;
+  int32_t pad;
+};
+struct TcPattern {
+  int32_t m, kpad, npad, tcols;  // DOFs, K and N padded for the MMA, TMEM columns
+  int64_t kc_off;                // K_p hi|lo in canonical layout (float offset)
+  int64_t lidx_off;              // local-index block of the pattern ([n_p][C_p])
+  int64_t cstart, ccount;        // sorted cells of the pattern
+};
+
 struct GraphCache {
   bool valid = false;
   double dt = 0, alpha = 0;
@@ -90,6 +109,18 @@ struct sbx_ctx {
   int n_tiles_simt = 0;
   int max_m = 0;
 
+  // tensor-core path (SBX_PREC_MIXED); tiles in launch classes by the
+  // shared memory they need
+  sbx::TcPattern *d_tc_pat = nullptr;
+  float *d_tc_K = nullptr;
+  uint16_t *d_tc_lidx = nullptr;
+  int32_t *d_tc_nodes = nullptr;
+  sbx::TcTile *d_tc_tiles[sbx::TC_CLASSES] = {};
+  int n_tc_tiles[sbx::TC_CLASSES] = {};
+  int tc_kmax[sbx::TC_CLASSES] = {}, tc_nmax[sbx::TC_CLASSES] = {};
+  int tc_maxnodes[sbx::TC_CLASSES] = {}, tc_maxnc[sbx::TC_CLASSES] = {};
+  size_t tc_smem[sbx::TC_CLASSES] = {};
+
   // loads
   int n_load = 0;
   int64_t *d_load_dof = nullptr;
@@ -120,4 +151,10 @@ cudaError_t launch_zero_fixed(const sbx_ctx *ctx, double *u, cudaStream_t s);
 // Opt every kernel into the shared-memory size it may need (call once per
 // device, outside stream capture).
 cudaError_t prepare_kernels();
+// kernels_tc.cu
+int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<int64_t> &conn_off,
+             const std::vector<int64_t> &cnt, const std::vector<int64_t> &start, std::string &err);
+cudaError_t prepare_tc_kernels();
+cudaError_t launch_force_tc(const sbx_ctx *ctx, const double *u, double *f, double dt,
+                            cudaStream_t s);
 }  // namespace sbx
