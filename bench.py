@@ -156,13 +156,18 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 2000 for fp64, 20000 otherwise)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 2000 if args.precision == "fp64" else 20000
+        if args.impl == "reference":
+            args.steps = 20
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -215,20 +220,31 @@ def main():
     pk, pk_src = peaks()
     flops = contraction_flops(nper)
     bytes_step = algorithmic_bytes_per_step(mesh, nper)
+    # the force kernel's own algorithmic bytes: U_n of every node (24 B) and
+    # the cell data (4 n_p + 9 B); the update kernel's: 32 B per DOF
+    bytes_force = 8 * mesh.n_dof + int(np.sum(4 * nper + 9))
+    bytes_update = 32 * mesh.n_dof
+    step_frac = (bytes_step / (t_force + t_update) / 1e9) / pk["hbm_gbs"]
     if args.precision == "fp64":
         ach = flops / t_force / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                 "kernel": "k_force_simt<double> (DFMA contraction)",
-                "peak_source": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)",
-                "hbm_frac_of_step": (bytes_step / (t_force + t_update) / 1e9) / pk["hbm_gbs"]}
+                "peak_source": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)"}
     else:
-        ach = bytes_step / (t_force + t_update) / 1e9
+        ach = bytes_force / t_force / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"], "traffic": None,
-                "kernel": "force + update of one step", "peak_source": pk_src}
+                "kernel": "k_force_tc (all launch classes of one step)" if args.precision == "mixed"
+                else "k_force_simt<float>",
+                "peak_source": "hbm_gbs " + pk_src,
+                "tensor_tflops": 3 * flops / t_force / 1e12 if args.precision == "mixed" else None}
+    roof["algorithmic_bytes_per_launch"] = bytes_force
     roof["force_ms"] = t_force * 1e3
     roof["update_ms"] = t_update * 1e3
+    roof["update_hbm_frac"] = (bytes_update / t_update / 1e9) / pk["hbm_gbs"]
+    roof["step_bytes"] = bytes_step
+    roof["step_hbm_frac"] = step_frac
 
     # end to end through the C ABI with host buffers: upload the state from
     # pinned host memory, run e2e_steps steps, read the field back
@@ -253,14 +269,17 @@ def main():
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/f64",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp64": "f64", "fp32": "f32 contraction, f64 state",
+                     "mixed": "tf32x3 contraction (f32 accumulate), f64 state"}[args.precision],
            "data": "synthetic",
            "config": {"workload": mesh.name + " (cube minus r=0.2 ball, levels 4-8, lognormal E)",
                       "cells": mesh.n_cells, "dof": mesh.n_dof, "patterns": len(S.masters),
                       "precision": args.precision, "dt": S.dt,
                       "l2": "per-step working set %.0f MB > L2; no flush" % (bytes_step / 1e6),
                       "parallelism": "replicas" if world > 1 else "1 GPU"},
-           "roofline": roof, "gpu_launches": 2 * args.steps, "clocks": clocks, "e2e": e2e}
+           "roofline": roof, "gpu_launches": L.sbx_query(S.ctx, L.SBX_Q_KERNELS_PER_STEP) * args.steps,
+           "clocks": clocks, "e2e": e2e}
 
     if rank == 0 and not args.no_cpu_baseline:
         cb, P, n_ref, u_ref = cpu_baseline(mesh)

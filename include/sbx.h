@@ -201,6 +201,18 @@ int sbx_profile(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha,
                 double *ms_force, double *ms_update);
 
 /*
+ * sbx_query: diagnostics about the uploaded mesh and the launch plan.
+ *   what = SBX_Q_KERNELS_PER_STEP  kernel launches per step (force + update)
+ *          SBX_Q_FORCE_LAUNCHES    force-kernel launches per step
+ *          SBX_Q_TILES             CTAs of all force launches of one step
+ *   Errors: SBX_ESTATE (no mesh), SBX_EINVAL (unknown item, NULL out).
+ */
+#define SBX_Q_KERNELS_PER_STEP 0
+#define SBX_Q_FORCE_LAUNCHES   1
+#define SBX_Q_TILES            2
+int sbx_query(sbx_ctx *ctx, int what, int64_t *out);
+
+/*
  * sbx_step_static: one undamped explicit step with no external load that
  * allocates nothing.  The paper has no counterpart; this entry point exists
  * for callers that cannot allocate device memory: code that runs while a

@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "SBX_OK", 1: "SBX_EINVAL", 2: "SBX_ENOMEM", 3: "SBX_ECUDA",
 # every symbol include/sbx.h declares
 EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patterns",
            "mesh_upload", "set_load", "set_initial", "step_n", "sbx_get_step", "sbx_set_step",
-           "read_field", "write_field", "sbx_profile", "sbx_step_static"]
+           "read_field", "write_field", "sbx_profile", "sbx_query", "sbx_step_static"]
+SBX_Q_KERNELS_PER_STEP, SBX_Q_FORCE_LAUNCHES, SBX_Q_TILES = 0, 1, 2
 SBX_STATIC_MAX_DOF = 4 * 1024 * 1024
 SBX_STATIC_MAX_PATTERNS = 144
 
@@ -63,6 +64,7 @@ def load(path: str = LIB_PATH):
         "write_field": [vp, i32, vp, i64],
         "sbx_profile": [vp, i64, dbl, dbl, C.POINTER(dbl), C.POINTER(dbl)],
         "sbx_step_static": [vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, dbl, vp, vp],
+        "sbx_query": [vp, i32, C.POINTER(i64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -143,6 +145,12 @@ def set_initial(ctx, u0, v0, dt, alpha=0.0):
 
 def step_n(ctx, n_steps, dt, alpha=0.0):
     _check(ctx, load().step_n(ctx, int(n_steps), float(dt), float(alpha)))
+
+
+def sbx_query(ctx, what) -> int:
+    n = C.c_int64()
+    _check(ctx, load().sbx_query(ctx, int(what), C.byref(n)))
+    return n.value
 
 
 def sbx_get_step(ctx) -> int:

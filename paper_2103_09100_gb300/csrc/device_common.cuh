@@ -11,9 +11,59 @@ namespace sbx {
 // op = 8 * perm_index + sign_bits; node by node u_master[r] =
 // (-1)^{bit r} u_cell[perm[r]] (permutations of (0,1,2), lexicographic).
 __device__ __forceinline__ int op_perm_of(int op, int r) {
-  // byte i holds permutation i with perm[r] in bits 2r..2r+1
-  const uint64_t tab = 0x061209211824ull;
-  return (int)((tab >> (8 * (op >> 3) + 2 * r)) & 3u);
+  // permutation i (lexicographic): perm[0] = i / 2, perm[1] from a 2-bit
+  // table, perm[2] = 3 - perm[0] - perm[1]
+  const int i = op >> 3;
+  const int p0 = i >> 1;
+  const int p1 = (int)((0x489u >> (2 * i)) & 3u);   // {1, 2, 0, 2, 0, 1}[i]
+  return r == 0 ? p0 : (r == 1 ? p1 : 3 - p0 - p1);
+}
+
+// 2^k as a float, k in [-126, 127].
+__device__ __forceinline__ float exp2i(int k) { return __int_as_float((k + 127) << 23); }
+
+// FP64 -> FP32 pair (hi, lo) with hi = x rounded to 24 significant bits
+// (ties away from zero) and lo = (x - hi) rounded to FP32, using integer
+// operations and FP32 multiplies only: GB300's FP64 pipe runs at ~1/64 of
+// FP32, and a displacement field is exactly zero away from the wave front,
+// so every case must stay off that pipe.
+//   |x| < 2^-103 (zero, subnormal, tiny): hi = lo = 0 (signed)
+//   2^-103 <= |x| < 2^-74:                 hi exact to 24 bits, lo = 0
+//   |x| >= 2^126, Inf, NaN:                hi = +-Inf or NaN, lo = 0
+__device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const unsigned int sgn = (unsigned int)(b >> 63) << 31;
+  if (e < 920) {
+    hi = __uint_as_float(sgn);
+    lo = hi;
+    return;
+  }
+  if (e > 1148) {
+    const bool nan = e == 0x7FF && (b & 0xFFFFFFFFFFFFFull) != 0;
+    hi = __uint_as_float(sgn | (nan ? 0x7FC00000u : 0x7F800000u));
+    lo = 0.0f;
+    return;
+  }
+  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long hm = (mant + (1ull << 28)) >> 29;           // <= 2^24
+  const int rem = (int)((long long)mant - (long long)(hm << 29));      // |rem| <= 2^28
+  float h = (float)(unsigned)hm * exp2i(e - 1046);
+  float l = e >= 949 ? (float)rem * exp2i(e - 1075) : 0.0f;
+  hi = __uint_as_float(__float_as_uint(h) ^ sgn);
+  lo = __uint_as_float(__float_as_uint(l) ^ sgn);
+}
+
+// FP32 -> FP64 by re-packing the bits (exact for normal numbers); zero and
+// subnormals give a signed zero, Inf and NaN keep their kind.
+__device__ __forceinline__ double f2d_bits(float x) {
+  const unsigned int b = __float_as_uint(x);
+  const unsigned int e = (b >> 23) & 0xFFu;
+  const unsigned long long s = (unsigned long long)(b >> 31) << 63;
+  if (e == 0u) return __longlong_as_double((long long)s);
+  const unsigned long long de = e == 255u ? 0x7FFull : (unsigned long long)(e + 896u);
+  const unsigned long long d = s | (de << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
 }
 
 // Eqs. (Ricker), (Triangle), (Lamb).

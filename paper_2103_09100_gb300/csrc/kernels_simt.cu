@@ -171,37 +171,50 @@ cudaError_t prepare_kernels() {
 }
 
 // ------------------------------------------------------------------ update
-// Eq. (DnMdiag) with f = R_int - R_ext:
-//   U_{n+1} = (-dt^2 M^-1 f + 2 U_n - (1 - a dt/2) U_{n-1}) / (1 + a dt/2),
-// written over U_{n-1}.  f is reset to zero for the next step (unless the
-// caller keeps it for read-back).  Thread 0 advances the device step index.
-__global__ void __launch_bounds__(256) k_update(int64_t nd, const double *__restrict__ minv,
+// Eq. (DnMdiag) with f = R_int - R_ext and w = dt^2 M^-1 / (1 + a dt/2):
+//   U_{n+1} = -w f + (2 U_n - (1 - a dt/2) U_{n-1}) / (1 + a dt/2),
+// written over U_{n-1}.  Undamped: two FP64 FMAs per DOF (GB300's FP64 pipe
+// runs at ~1/64 of FP32, so the update is kept at the minimum FP64 work).
+// f is reset to zero for the next step (unless the caller keeps it for
+// read-back).  Thread 0 advances the device step index.
+__device__ __forceinline__ bool nonfinite(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF;
+}
+
+template <bool DAMPED>
+__device__ __forceinline__ double cdm_update(double w, double f, double uc, double up, double a,
+                                             double b) {
+  if (DAMPED) return fma(-w, f, fma(a, uc, -b * up));
+  return fma(-w, f, fma(2.0, uc, -up));
+}
+
+template <bool DAMPED>
+__global__ void __launch_bounds__(256) k_update(int64_t nd, const double *__restrict__ w,
                                                 double *__restrict__ f,
                                                 const double *__restrict__ uc,
-                                                double *__restrict__ up, double dt2, double cm,
-                                                double inv_cp, int zero_f, int32_t *flags,
-                                                int64_t *d_step) {
+                                                double *__restrict__ up, double a, double b,
+                                                int zero_f, int32_t *flags, int64_t *d_step) {
   bool bad = false;
   const int64_t n2 = nd / 2;
   const double2 *f2 = reinterpret_cast<const double2 *>(f);
-  const double2 *m2 = reinterpret_cast<const double2 *>(minv);
+  const double2 *w2 = reinterpret_cast<const double2 *>(w);
   const double2 *c2 = reinterpret_cast<const double2 *>(uc);
   double2 *p2 = reinterpret_cast<double2 *>(up);
   double2 *fz = reinterpret_cast<double2 *>(f);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double2 fv = f2[i], mv = m2[i], cv = c2[i], pv = p2[i];
+    const double2 fv = f2[i], wv = w2[i], cv = c2[i], pv = p2[i];
     double2 r;
-    r.x = (-dt2 * mv.x * fv.x + 2.0 * cv.x - cm * pv.x) * inv_cp;
-    r.y = (-dt2 * mv.y * fv.y + 2.0 * cv.y - cm * pv.y) * inv_cp;
-    bad |= !isfinite(r.x) || !isfinite(r.y);
+    r.x = cdm_update<DAMPED>(wv.x, fv.x, cv.x, pv.x, a, b);
+    r.y = cdm_update<DAMPED>(wv.y, fv.y, cv.y, pv.y, a, b);
+    bad |= nonfinite(r.x) || nonfinite(r.y);
     p2[i] = r;
     if (zero_f) fz[i] = make_double2(0.0, 0.0);
   }
   if ((nd & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     const int64_t d = nd - 1;
-    const double r = (-dt2 * minv[d] * f[d] + 2.0 * uc[d] - cm * up[d]) * inv_cp;
-    bad |= !isfinite(r);
+    const double r = cdm_update<DAMPED>(w[d], f[d], uc[d], up[d], a, b);
+    bad |= nonfinite(r);
     up[d] = r;
     if (zero_f) f[d] = 0.0;
   }
@@ -216,12 +229,36 @@ static int update_grid(int64_t nd) {
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
+__global__ void k_make_w(int64_t nd, const double *minv, double *w, double c) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd;
+       i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = c * minv[i];
+}
+
+cudaError_t prepare_update(sbx_ctx *ctx, double dt, double alpha, cudaStream_t s) {
+  if (ctx->w_valid && ctx->w_dt == dt && ctx->w_alpha == alpha) return cudaSuccess;
+  const int64_t nd = ctx->ndof * ctx->B;
+  const double cp = 1.0 + 0.5 * alpha * dt;
+  k_make_w<<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_minv, ctx->d_w, dt * dt / cp);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    ctx->w_valid = true;
+    ctx->w_dt = dt;
+    ctx->w_alpha = alpha;
+  }
+  return e;
+}
+
 cudaError_t launch_update(const sbx_ctx *ctx, const double *uc, double *up, double *f, double dt,
                           double alpha, int zero_f, cudaStream_t s) {
   const int64_t nd = ctx->ndof * ctx->B;
   const double cm = 1.0 - 0.5 * alpha * dt, cp = 1.0 + 0.5 * alpha * dt;
-  k_update<<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_minv, f, uc, up, dt * dt, cm, 1.0 / cp,
-                                           zero_f, ctx->d_flags, ctx->d_step);
+  if (alpha == 0.0)
+    k_update<false><<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_w, f, uc, up, 2.0, 1.0, zero_f,
+                                                    ctx->d_flags, ctx->d_step);
+  else
+    k_update<true><<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_w, f, uc, up, 2.0 / cp, cm / cp,
+                                                   zero_f, ctx->d_flags, ctx->d_step);
   return cudaGetLastError();
 }
 

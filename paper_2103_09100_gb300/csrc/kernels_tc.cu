@@ -1,22 +1,33 @@
-// Mixed-precision internal force on the 5th-generation tensor cores.
+// Mixed-precision internal force on the 5th-generation tensor cores:
+// a persistent, software-pipelined kernel.
 //
-// Per CTA: one tile of up to 128 cells of one pattern p (m = 3 n_p DOFs).
-//   1. The tile's unique nodes (host-sorted list) are gathered once into
-//      shared memory (FP64); each (cell, slot) refers to them through a
-//      16-bit local index, which replaces the 32-bit connectivity.
-//   2. A (128 x K) = transformed cell displacements, each minus the
-//      displacement of the cell's first node (K_p annihilates translations,
-//      so the difference is exact in FP64 and only the deformation part is
-//      rounded), split into TF32 hi + lo.
-//   3. D (TMEM, 128 x N, FP32) = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T with
-//      B = K_p split the same way (tcgen05.mma kind::tf32, issued by one
-//      thread, completion through tcgen05.commit -> mbarrier).
-//   4. Epilogue: tcgen05.ld rows of D (row = cell), scale by E_e h_e in FP64,
-//      back-transform (Q^T), accumulate per unique node in shared memory
-//      (FP64), then one global FP64 atomic per unique node DOF.
+// Work unit: a tile of up to 128 cells of one pattern p (m = 3 n_p DOFs) and
+// the tile's unique nodes.  The host packs each tile into one contiguous
+// record (layout below) that replaces the connectivity.  Each CTA (128
+// threads) walks tiles blockIdx.x, +gridDim.x, ... with two stages:
+//   * the record of tile i+2 streams in by one 1-D bulk copy (TMA engine,
+//     completion on an mbarrier) and the displacements of tile i+1's nodes by
+//     per-thread cp.async, while tile i is computed;
+//   * tile i: A (128 x K) = each cell's displacements, transformed by its op
+//     (Sec. 3.2.2) and minus its slot-0 node's displacement (K_p annihilates
+//     translations), formed in FP32 from a bit-level FP64 -> (hi, lo) split,
+//     rounded to TF32 hi + lo;  D (TMEM) = A_hi B_hi^T + A_hi B_lo^T +
+//     A_lo B_hi^T with B = K_p split the same way (tcgen05.mma kind::tf32 by
+//     one thread, completion by tcgen05.commit -> mbarrier);  tcgen05.ld D
+//     (row = cell) times E_e h_e;  per node, sum Q^T F over its incidences in
+//     FP32 and add it with one FP64 atomic per DOF.
+// No FP64 arithmetic runs per incidence (GB300's FP64 pipe is ~1/64 of FP32).
 // Operands use the canonical no-swizzle K-major layout: 8-row x 16-byte core
-// matrices, row groups stored one after another (stride nK * 128 B), K groups
-// 128 B apart inside a row group.
+// matrices, row groups nK * 128 B apart, K groups 128 B apart within a row
+// group (LBO = 128 B, SBO = nK * 128 B).
+//
+// Record layout (every part padded to 16 bytes):
+//   int32 {pat, ncell, nn, n}          header (16 B)
+//   uint8 sym[ncell]                   op of each cell
+//   float scale[ncell]                 E_e h_e rounded to FP32
+//   int32 nodes[nn]                    unique node ids, ascending
+//   uint16 off[nn + 1]                 incidence offsets per node
+//   uint16 inc[n * ncell]              incidences (cell << 5 | slot) by node
 #include <math.h>
 #include <string.h>
 
@@ -32,195 +43,329 @@ namespace sbx {
 
 namespace {
 
+constexpr int TC_THREADS = 128;
 constexpr uint32_t WAIT_POLLS = 1u << 22;
 
-struct SmemLayout {
-  uint32_t B, A, ucache, fnode, lidx, cell, total;
+__host__ __device__ inline uint32_t a16(uint32_t x) { return (x + 15u) & ~15u; }
+__host__ __device__ inline uint32_t a128(uint32_t x) { return (x + 127u) & ~127u; }
+
+struct RecLayout {
+  uint32_t sym, scale, nodes, off, inc, bytes;
 };
+__host__ __device__ inline RecLayout rec_layout(int ncell, int nn, int n) {
+  RecLayout R;
+  uint32_t o = 16;
+  R.sym = o;   o += a16((uint32_t)ncell);
+  R.scale = o; o += a16(4u * ncell);
+  R.nodes = o; o += a16(4u * nn);
+  R.off = o;   o += a16(2u * (nn + 1));
+  R.inc = o;   o += a16(2u * n * ncell);
+  R.bytes = o;
+  return R;
+}
 
-__host__ __device__ inline uint32_t align128(uint32_t x) { return (x + 127u) & ~127u; }
-
-__host__ __device__ inline SmemLayout layout(int kmax, int nmax, int max_nodes, int nmax_nodes_cell) {
+struct SmemLayout {
+  uint32_t B, A, ref, stage[2], u_off, total;
+};
+// kmax, nmax: padded K and N; rec_max: largest record; nn_max: most nodes
+__host__ __device__ inline SmemLayout smem_layout(int kmax, int nmax, int rec_max, int nn_max) {
   SmemLayout L;
-  uint32_t off = 128;                                   // mbarrier + TMEM address
-  L.B = off;      off = align128(off + 2u * nmax * kmax * 4u);
-  L.A = off;      off = align128(off + 2u * 128u * kmax * 4u);
-  L.ucache = off; off = align128(off + (uint32_t)max_nodes * 24u);
-  L.fnode = off;  off = align128(off + (uint32_t)max_nodes * 24u);
-  L.lidx = off;   off = align128(off + (uint32_t)nmax_nodes_cell * 128u * 2u);
-  L.cell = off;   off = align128(off + 128u * 8u + 128u);
-  L.total = off;
+  uint32_t o = 128;                                    // 3 mbarriers + TMEM address
+  L.B = o;   o = a128(o + 2u * nmax * kmax * 4u);
+  L.A = o;   o = a128(o + 2u * 128u * kmax * 4u);
+  L.ref = o; o = a128(o + 128u * ((kmax + 2) / 3) * 2u);  // lid[slot][cell], uint16
+  L.u_off = a16((uint32_t)rec_max);
+  const uint32_t st = a128(L.u_off + 24u * (uint32_t)nn_max);
+  L.stage[0] = o; o += st;
+  L.stage[1] = o; o += st;
+  L.total = o;
   return L;
 }
 
-__global__ void __launch_bounds__(256, 1)
-    k_force_tc(const TcTile *__restrict__ tiles, const TcPattern *__restrict__ pats,
-               const int32_t *__restrict__ tile_nodes, const uint16_t *__restrict__ lidx,
-               const float *__restrict__ Kc, const uint8_t *__restrict__ sym,
-               const double *__restrict__ scale, const double *__restrict__ u,
-               double *__restrict__ f, LoadTable Ld, const int64_t *__restrict__ d_step,
-               double dt, int32_t *flags, int kmax, int nmax, int max_nodes, int nmax_nodes_cell) {
+struct Stage {
+  const int32_t *hdr;
+  const uint8_t *sym;
+  const float *scale;
+  const int32_t *nodes;
+  const uint16_t *off, *inc;
+  double *u;
+};
+__device__ inline Stage stage_view(unsigned char *base, uint32_t u_off) {
+  Stage S;
+  S.hdr = reinterpret_cast<const int32_t *>(base);
+  const RecLayout R = rec_layout(S.hdr[1], S.hdr[2], S.hdr[3]);
+  S.sym = base + R.sym;
+  S.scale = reinterpret_cast<const float *>(base + R.scale);
+  S.nodes = reinterpret_cast<const int32_t *>(base + R.nodes);
+  S.off = reinterpret_cast<const uint16_t *>(base + R.off);
+  S.inc = reinterpret_cast<const uint16_t *>(base + R.inc);
+  S.u = reinterpret_cast<double *>(base + u_off);
+  return S;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 4)
+    k_force_tc(const TcTile *__restrict__ tiles, int ntiles, const uint8_t *__restrict__ recs,
+               const TcPattern *__restrict__ pats, const float *__restrict__ Kc,
+               const double *__restrict__ u, double *__restrict__ f, LoadTable Ld,
+               const int64_t *__restrict__ d_step, double dt, int32_t *flags, int kmax, int nmax,
+               int rec_max, int nn_max, int tcols) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const SmemLayout SL = layout(kmax, nmax, max_nodes, nmax_nodes_cell);
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
-  uint32_t *taddr_s = reinterpret_cast<uint32_t *>(smem + 8);
+  const SmemLayout SL = smem_layout(kmax, nmax, rec_max, nn_max);
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [0] MMA, [1], [2] records
+  uint32_t *taddr_s = reinterpret_cast<uint32_t *>(smem + 32);
   float *Bs = reinterpret_cast<float *>(smem + SL.B);
   float *As = reinterpret_cast<float *>(smem + SL.A);
-  double *ucache = reinterpret_cast<double *>(smem + SL.ucache);
-  double *fnode = reinterpret_cast<double *>(smem + SL.fnode);
-  uint16_t *lid = reinterpret_cast<uint16_t *>(smem + SL.lidx);
-  double *scale_s = reinterpret_cast<double *>(smem + SL.cell);
-  uint8_t *sym_s = smem + SL.cell + 128 * 8;
-
+  uint16_t *lid = reinterpret_cast<uint16_t *>(smem + SL.ref);   // [slot][cell]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const TcTile T = tiles[blockIdx.x];
-  const TcPattern P = pats[T.pat];
-  const int m = P.m, n = m / 3, kpad = P.kpad, npad = P.npad, nK = kpad / 4;
-  const int ncell = T.ncell;
-  const int64_t gbase = P.cstart + T.cell0;
+  const int G = gridDim.x;
+  const uint32_t mb_mma = tc::smem_addr(&mbar[0]);
+  const uint32_t mb_rec0 = tc::smem_addr(&mbar[1]);   // stage s: mb_rec0 + 8 s
 
   if (warp == 0) {
-    tc::tmem_alloc(tc::smem_addr(taddr_s), (uint32_t)P.tcols);
+    tc::tmem_alloc(tc::smem_addr(taddr_s), (uint32_t)tcols);
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(tc::smem_addr(mbar), 1);
+    tc::mbar_init(mb_mma, 1);
+    tc::mbar_init(mb_rec0, 1);
+    tc::mbar_init(mb_rec0 + 8u, 1);
     tc::mbar_fence_init();
   }
-  // B = K_p hi | lo, stored in canonical layout in global memory
-  {
-    const float4 *src = reinterpret_cast<const float4 *>(Kc + P.kc_off);
-    float4 *dst = reinterpret_cast<float4 *>(Bs);
-    const int nv = (2 * npad * kpad) / 4;
-    for (int i = tid; i < nv; i += 256) dst[i] = src[i];
+  if (blockIdx.x == 0 && Ld.n > 0) {   // external load of this step (Sec. 5)
+    const double t = (double)(*d_step) * dt;
+    for (int l = tid; l < Ld.n; l += TC_THREADS)
+      atomicAdd(&f[Ld.dof[l]], -Ld.amp[l] * wavelet_value(Ld.kind[l], t, Ld.t1[l], Ld.ncyc[l]));
   }
-  for (int c = tid; c < ncell; c += 256) {
-    sym_s[c] = sym[gbase + c];
-    scale_s[c] = scale[gbase + c];
-  }
-  for (int i = tid; i < T.n_nodes; i += 256) {
-    const int64_t node = tile_nodes[T.node_off + i];
-    ucache[3 * i + 0] = u[3 * node + 0];
-    ucache[3 * i + 1] = u[3 * node + 1];
-    ucache[3 * i + 2] = u[3 * node + 2];
-    fnode[3 * i + 0] = 0.0;
-    fnode[3 * i + 1] = 0.0;
-    fnode[3 * i + 2] = 0.0;
-  }
-  for (int idx = tid; idx < n * 128; idx += 256) {
-    const int k = idx >> 7, c = idx & 127;
-    if (c < ncell) lid[idx] = lidx[P.lidx_off + (int64_t)k * P.ccount + T.cell0 + c];
-  }
-  __syncthreads();
-
-  // A: row c, column 3k + r  ->  byte (c/8)*nK*128 + (col/4)*128 + (c%8)*16 + (col%4)*4
-  float *Ahi = As, *Alo = As + 128 * kpad;
-  for (int idx = tid; idx < n * 128; idx += 256) {
-    const int k = idx >> 7, c = idx & 127;
-    if (c >= ncell) continue;
-    const int op = sym_s[c];
-    const int li = lid[idx], l0 = lid[c];
-    const int rowoff = (c >> 3) * nK * 32 + (c & 7) * 4;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const int a = op_perm_of(op, r);
-      const double sg = ((op >> r) & 1) ? -1.0 : 1.0;
-      const float x = (float)(sg * (ucache[3 * li + a] - ucache[3 * l0 + a]));
-      const float hi = tc::to_tf32(x);
-      const float lo = tc::to_tf32(x - hi);
-      const int col = 3 * k + r;
-      const int off = rowoff + (col >> 2) * 32 + (col & 3);
-      Ahi[off] = hi;
-      Alo[off] = lo;
-    }
-  }
-  for (int idx = tid; idx < (kpad - m) * 128; idx += 256) {   // zero K padding
-    const int col = m + idx / 128, c = idx % 128;
-    const int off = (c >> 3) * nK * 32 + (c & 7) * 4 + (col >> 2) * 32 + (col & 3);
-    Ahi[off] = 0.0f;
-    Alo[off] = 0.0f;
-  }
-  tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = *taddr_s;
-  const uint32_t mbar_a = tc::smem_addr(mbar);
 
-  if (tid == 0) {
-    const uint32_t idesc = tc::idesc_tf32(128, npad);
-    const uint32_t a_hi = tc::smem_addr(Ahi), a_lo = tc::smem_addr(Alo);
-    const uint32_t b_hi = tc::smem_addr(Bs), b_lo = tc::smem_addr(Bs + npad * kpad);
-    const uint32_t sbo = (uint32_t)nK * 128u;
-    for (int s = 0; s < kpad / 8; ++s) {
-      const uint32_t o = (uint32_t)s * 256u;
-      const uint64_t ah = tc::smem_desc(a_hi + o, 128, sbo), al = tc::smem_desc(a_lo + o, 128, sbo);
-      const uint64_t bh = tc::smem_desc(b_hi + o, 128, sbo), bl = tc::smem_desc(b_lo + o, 128, sbo);
-      tc::mma_tf32(taddr, ah, bh, idesc, s > 0 ? 1u : 0u);
-      tc::mma_tf32(taddr, ah, bl, idesc, 1u);
-      tc::mma_tf32(taddr, al, bh, idesc, 1u);
+  auto issue_record = [&](int s, int tile) {   // thread 0 only
+    const TcTile T = tiles[tile];
+    tc::fence_proxy_async_smem();
+    const uint32_t mb = mb_rec0 + 8u * (uint32_t)s;
+    tc::mbar_arrive_expect_tx(mb, (uint32_t)T.rec_bytes);
+    tc::bulk_g2s(tc::smem_addr(smem + (s ? SL.stage[1] : SL.stage[0])), recs + T.rec_off,
+                 (uint32_t)T.rec_bytes, mb);
+  };
+  auto issue_gather = [&](int s) {            // all threads
+    const Stage S = stage_view(smem + (s ? SL.stage[1] : SL.stage[0]), SL.u_off);
+    const int nn = S.hdr[2];
+    const uint32_t ub = tc::smem_addr(S.u);
+    for (int i = tid; i < nn; i += TC_THREADS) {
+      const double *src = u + 3 * (int64_t)S.nodes[i];
+      tc::cp_async8(ub + 24u * i, src);
+      tc::cp_async8(ub + 24u * i + 8u, src + 1);
+      tc::cp_async8(ub + 24u * i + 16u, src + 2);
     }
-    tc::mma_commit(mbar_a);
-  }
-  bool ok = tc::mbar_wait_bounded(mbar_a, 0, WAIT_POLLS);
-  ok = __syncthreads_and(ok);
-  tc::fence_after_sync();
-  if (!ok) {
-    if (tid == 0) atomicOr(flags, 2);
-    tc::mbar_wait_bounded(mbar_a, 0, WAIT_POLLS);   // let in-flight MMAs drain
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(taddr, (uint32_t)P.tcols);
-    return;
-  }
+    tc::cp_async_commit();
+  };
 
-  // epilogue: D row = cell.  Warps w and w+4 share lanes 32*(w%4).. and
-  // split the columns.  F (FP32, row stride npad+1) overwrites A.
-  float *F = As;
-  const int half = npad / 2;
-  {
-    const int c = 32 * (warp & 3) + lane;
-    const int col0 = (warp >> 2) * half;
-    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    for (int cc = col0; cc < col0 + half; cc += 8) {
-      float v[8];
-      tc::tmem_ld8(taddr + lane_base + (uint32_t)cc, v);
-      tc::tmem_ld_wait();
-      if (c < ncell) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-          if (cc + i < m) F[c * (npad + 1) + cc + i] = v[i];
+  // bit s of ph_rec / pend: parity and "copy in flight" of stage s's record
+  uint32_t ph_rec = 0u, pend = 0u, ph_mma = 0u;
+  bool ok = true;
+  int tile = blockIdx.x;
+  if (tile < ntiles) {
+    if (tid == 0) {
+      issue_record(0, tile);
+      if (tile + G < ntiles) issue_record(1, tile + G);
+    }
+    pend = 1u | (tile + G < ntiles ? 2u : 0u);
+    ok = __syncthreads_and(tc::mbar_wait_bounded(mb_rec0, ph_rec & 1u, WAIT_POLLS));
+    if (ok) {
+      ph_rec ^= 1u;
+      pend &= ~1u;
+      issue_gather(0);
+    }
+  }
+  int cur_pat = -1;
+  for (int i = 0; ok && tile < ntiles; ++i, tile += G) {
+    const int s = i & 1;
+    const uint32_t so = (uint32_t)(s ^ 1);
+    tc::cp_async_wait_all();
+    __syncthreads();
+    const int next = tile + G;
+    if (next < ntiles) {
+      ok = __syncthreads_and(
+          tc::mbar_wait_bounded(mb_rec0 + 8u * so, (ph_rec >> so) & 1u, WAIT_POLLS));
+      if (!ok) break;
+      ph_rec ^= 1u << so;
+      pend &= ~(1u << so);
+      issue_gather(s ^ 1);
+    }
+    const Stage S = stage_view(smem + (s ? SL.stage[1] : SL.stage[0]), SL.u_off);
+    const int pat = S.hdr[0], ncell = S.hdr[1], nn = S.hdr[2];
+    const TcPattern P = pats[pat];
+    const int m = P.m, kpad = P.kpad, npad = P.npad, nK = kpad / 4;
+    if (pat != cur_pat) {   // B = K_p hi | lo, canonical layout
+      const float4 *src = reinterpret_cast<const float4 *>(Kc + P.kc_off);
+      float4 *dst = reinterpret_cast<float4 *>(Bs);
+      const int nv = (2 * npad * kpad) / 4;
+      for (int q = tid; q < nv; q += TC_THREADS) dst[q] = src[q];
+      cur_pat = pat;
+    }
+    // phase S (per node): split U_n in place into FP32 (hi xyz, lo xyz) and
+    // record the node's local index for each of its (cell, slot) incidences
+    const int n = m / 3;
+    {
+      float *uf = reinterpret_cast<float *>(S.u);
+      for (int q = tid; q < nn; q += TC_THREADS) {
+        const double x0 = S.u[3 * q], x1 = S.u[3 * q + 1], x2 = S.u[3 * q + 2];
+        float h0, h1, h2, l0, l1, l2;
+        split_f64(x0, h0, l0);
+        split_f64(x1, h1, l1);
+        split_f64(x2, h2, l2);
+        float *o = uf + 6 * q;
+        o[0] = h0; o[1] = h1; o[2] = h2; o[3] = l0; o[4] = l1; o[5] = l2;
+        for (int j = S.off[q]; j < S.off[q + 1]; ++j) {
+          const int e = S.inc[j];
+          lid[(e & 31) * 128 + (e >> 5)] = (uint16_t)q;
+        }
       }
     }
+    __syncthreads();
+    // phase A (per cell, row c): d = (hi - hi_ref) + (lo - lo_ref) in FP32 with
+    // the slot-0 node as reference (the hi difference of nearby values is
+    // exact), transformed by the cell's op, split into TF32 hi + lo.
+    // A(c, col) -> float (c/8)*nK*32 + (c%8)*4 + (col/4)*32 + col%4; four
+    // nodes = 12 columns = three float4 stores per operand.
+    float *Ahi = As, *Alo = As + 128 * kpad;
+    const int nk4 = (kpad + 11) / 12;   // groups of four nodes (12 columns)
+    for (int w = tid; w < ncell * nk4; w += TC_THREADS) {
+      const int c = w % ncell, k4 = w / ncell;
+      const int op = S.sym[c];
+      const int p0 = op_perm_of(op, 0), p1 = op_perm_of(op, 1), p2 = op_perm_of(op, 2);
+      const float s0 = (op & 1) ? -1.0f : 1.0f, s1 = (op & 2) ? -1.0f : 1.0f,
+                  s2 = (op & 4) ? -1.0f : 1.0f;
+      const float *uf = reinterpret_cast<const float *>(S.u);
+      const float *rf = uf + 6 * lid[c];
+      const float rh[3] = {rf[0], rf[1], rf[2]}, rl[3] = {rf[3], rf[4], rf[5]};
+      const int rowoff = (c >> 3) * nK * 32 + (c & 7) * 4;
+      {
+        float vh[12], vl[12];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int k = 4 * k4 + t;
+          float d[3] = {0.0f, 0.0f, 0.0f};
+          if (k < n) {
+            const float *nf = uf + 6 * lid[k * 128 + c];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) d[a] = (nf[a] - rh[a]) + (nf[3 + a] - rl[a]);
+          }
+          const float x[3] = {s0 * (p0 == 0 ? d[0] : (p0 == 1 ? d[1] : d[2])),
+                              s1 * (p1 == 0 ? d[0] : (p1 == 1 ? d[1] : d[2])),
+                              s2 * (p2 == 0 ? d[0] : (p2 == 1 ? d[1] : d[2]))};
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            vh[3 * t + r] = tc::to_tf32(x[r]);
+            vl[3 * t + r] = tc::to_tf32(x[r] - vh[3 * t + r]);
+          }
+        }
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+          const int q4 = 3 * k4 + g;            // float4 column group
+          if (4 * q4 < kpad) {
+            const int o = rowoff + q4 * 32;
+            *reinterpret_cast<float4 *>(Ahi + o) =
+                make_float4(vh[4 * g], vh[4 * g + 1], vh[4 * g + 2], vh[4 * g + 3]);
+            *reinterpret_cast<float4 *>(Alo + o) =
+                make_float4(vl[4 * g], vl[4 * g + 1], vl[4 * g + 2], vl[4 * g + 3]);
+          }
+        }
+      }
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      const uint32_t idesc = tc::idesc_tf32(128, npad);
+      const uint32_t a_hi = tc::smem_addr(Ahi), a_lo = tc::smem_addr(Alo);
+      const uint32_t b_hi = tc::smem_addr(Bs), b_lo = tc::smem_addr(Bs + npad * kpad);
+      const uint32_t sbo = (uint32_t)nK * 128u;
+      for (int ks = 0; ks < kpad / 8; ++ks) {
+        const uint32_t o = (uint32_t)ks * 256u;
+        const uint64_t ah = tc::smem_desc(a_hi + o, 128, sbo), al = tc::smem_desc(a_lo + o, 128, sbo);
+        const uint64_t bh = tc::smem_desc(b_hi + o, 128, sbo), bl = tc::smem_desc(b_lo + o, 128, sbo);
+        tc::mma_tf32(taddr, ah, bh, idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32(taddr, ah, bl, idesc, 1u);
+        tc::mma_tf32(taddr, al, bh, idesc, 1u);
+      }
+      tc::mma_commit(mb_mma);
+    }
+    ok = __syncthreads_and(tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_POLLS));
+    tc::fence_after_sync();
+    if (!ok) break;
+    ph_mma ^= 1u;
+    // epilogue: warp w holds TMEM lanes 32w..32w+31 (cells); F = E h D
+    // (FP32, row stride npad + 1) overwrites A
+    float *F = As;
+    {
+      const int c = 32 * warp + lane;
+      const float sc = c < ncell ? S.scale[c] : 0.0f;
+      const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+      for (int cc = 0; cc < npad; cc += 8) {
+        float v[8];
+        tc::tmem_ld8(taddr + lane_base + (uint32_t)cc, v);
+        tc::tmem_ld_wait();
+        if (c < ncell) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (cc + q < m) F[c * (npad + 1) + cc + q] = sc * v[q];
+        }
+      }
+      // back to the cell frame, node by node: f_cell[perm r] = sign_r f_master[r]
+      if (c < ncell) {
+        const int op = S.sym[c];
+        const int p0 = op_perm_of(op, 0), p1 = op_perm_of(op, 1), p2 = op_perm_of(op, 2);
+        float *Fr = F + c * (npad + 1);
+        for (int k = 0; k < m / 3; ++k) {
+          const float v0 = (op & 1) ? -Fr[3 * k] : Fr[3 * k];
+          const float v1 = (op & 2) ? -Fr[3 * k + 1] : Fr[3 * k + 1];
+          const float v2 = (op & 4) ? -Fr[3 * k + 2] : Fr[3 * k + 2];
+          Fr[3 * k + p0] = v0;
+          Fr[3 * k + p1] = v1;
+          Fr[3 * k + p2] = v2;
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // node sums (FP32; below the TF32x3 contraction error) and one FP64
+    // atomic per node DOF
+    for (int q = tid; q < nn; q += TC_THREADS) {
+      float acc[3] = {0.0f, 0.0f, 0.0f};
+      for (int j = S.off[q]; j < S.off[q + 1]; ++j) {
+        const int e = S.inc[j];
+        const float *Fr = F + (e >> 5) * (npad + 1) + 3 * (e & 31);
+        acc[0] += Fr[0];
+        acc[1] += Fr[1];
+        acc[2] += Fr[2];
+      }
+      double *fn = f + 3 * (int64_t)S.nodes[q];
+      atomicAdd(fn + 0, f2d_bits(acc[0]));
+      atomicAdd(fn + 1, f2d_bits(acc[1]));
+      atomicAdd(fn + 2, f2d_bits(acc[2]));
+    }
+    __syncthreads();   // stage s and F are free
+    if (next + G < ntiles) {
+      if (tid == 0) issue_record(s, next + G);
+      pend |= 1u << s;
+    }
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(flags, 2);
+    // let in-flight copies and MMAs drain before the CTA leaves
+    tc::cp_async_wait_all();
+    if (pend & 1u) tc::mbar_wait_bounded(mb_rec0, ph_rec & 1u, WAIT_POLLS);
+    if (pend & 2u) tc::mbar_wait_bounded(mb_rec0 + 8u, (ph_rec >> 1) & 1u, WAIT_POLLS);
+    tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_POLLS);
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(taddr, (uint32_t)P.tcols);
-
-  for (int idx = tid; idx < n * 128; idx += 256) {
-    const int k = idx >> 7, c = idx & 127;
-    if (c >= ncell) continue;
-    const int op = sym_s[c];
-    const int li = lid[idx];
-    const double s = scale_s[c];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const double sg = ((op >> r) & 1) ? -s : s;
-      atomicAdd(&fnode[3 * li + op_perm_of(op, r)], sg * (double)F[c * (npad + 1) + 3 * k + r]);
-    }
-  }
-  __syncthreads();
-  for (int i = tid; i < T.n_nodes; i += 256) {
-    const int64_t node = tile_nodes[T.node_off + i];
-    atomicAdd(&f[3 * node + 0], fnode[3 * i + 0]);
-    atomicAdd(&f[3 * node + 1], fnode[3 * i + 1]);
-    atomicAdd(&f[3 * node + 2], fnode[3 * i + 2]);
-  }
-  if (blockIdx.x == 0 && Ld.n > 0) {
-    const double t = (double)(*d_step) * dt;
-    for (int l = tid; l < Ld.n; l += 256)
-      atomicAdd(&f[Ld.dof[l]], -Ld.amp[l] * wavelet_value(Ld.kind[l], t, Ld.t1[l], Ld.ncyc[l]));
-  }
+  if (warp == 0) tc::tmem_dealloc(taddr, (uint32_t)tcols);
 }
 
 float tf32_round_host(float x) {
@@ -234,25 +379,32 @@ float tf32_round_host(float x) {
   return r;
 }
 
+template <typename T>
+void put(std::vector<uint8_t> &buf, size_t at, const T *src, size_t n) {
+  memcpy(buf.data() + at, src, n * sizeof(T));
+}
+
 }  // namespace
 
-// Host preparation of the tile lists, local indices and canonical K_p.
+// Host preparation of the tile records and canonical K_p.
 int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<int64_t> &conn_off,
-             const std::vector<int64_t> &cnt, const std::vector<int64_t> &start, std::string &err) {
+             const std::vector<int64_t> &cnt, const std::vector<int64_t> &start,
+             const std::vector<uint8_t> &sym_sorted, const std::vector<double> &scale_sorted,
+             std::string &err) {
   const int P = ctx->n_pat;
   std::vector<TcPattern> pats(P);
   std::vector<float> Kc;
-  std::vector<uint16_t> lidx(std::max<size_t>(conn.size(), 1));
-  std::vector<int32_t> nodes;
-  // launch classes by the tile's own shared-memory need: <= 56 KB (4 CTAs
-  // per SM), <= 113 KB (2 per SM), larger (1 per SM)
+  std::vector<uint8_t> recs;
+  // launch classes by a tile's own shared-memory need (double-buffered
+  // records and gathers): <= 56 KB, <= 113 KB, larger
   std::vector<TcTile> tiles[TC_CLASSES];
-  int kmax[TC_CLASSES], nmax[TC_CLASSES], maxn[TC_CLASSES], maxnc[TC_CLASSES];
+  int kmax[TC_CLASSES], nmax[TC_CLASSES], recmax[TC_CLASSES], nnmax[TC_CLASSES], tcols[TC_CLASSES];
   for (int c = 0; c < TC_CLASSES; ++c) {
     kmax[c] = 8;
     nmax[c] = 16;
-    maxn[c] = 1;
-    maxnc[c] = 8;
+    recmax[c] = 16;
+    nnmax[c] = 1;
+    tcols[c] = 32;
   }
   const uint32_t class_limit[TC_CLASSES] = {56u * 1024u, 113u * 1024u, 227u * 1024u};
   for (int p = 0; p < P; ++p) {
@@ -263,7 +415,7 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
     tp.npad = (m + 15) / 16 * 16;
     tp.tcols = tp.npad <= 32 ? 32 : (tp.npad <= 64 ? 64 : 128);
     tp.kc_off = (int64_t)Kc.size();
-    tp.lidx_off = conn_off[p];
+    tp.lidx_off = 0;
     tp.cstart = start[p];
     tp.ccount = cnt[p];
     const int nK = tp.kpad / 4;
@@ -273,44 +425,57 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
         const double kv = ctx->K_host[ctx->pat_koff[p] + (int64_t)i * m + j];
         const float hi = tf32_round_host((float)kv);
         const float lo = tf32_round_host((float)(kv - (double)hi));
-        const size_t off = (size_t)(i >> 3) * nK * 32 + (j >> 2) * 32 + (i & 7) * 4 + (j & 3);
-        B[off] = hi;
-        B[(size_t)tp.npad * tp.kpad + off] = lo;
+        const size_t o = (size_t)(i >> 3) * nK * 32 + (j >> 2) * 32 + (i & 7) * 4 + (j & 3);
+        B[o] = hi;
+        B[(size_t)tp.npad * tp.kpad + o] = lo;
       }
     Kc.insert(Kc.end(), B.begin(), B.end());
     if (cnt[p] == 0) continue;
-    const int per = m <= 36 ? 128 : 64;
-    std::vector<std::pair<int32_t, int32_t>> v;   // (node, k * C_p + j)
+    // dense, frequent small patterns: 128 cells per tile; others (rarer,
+    // scattered, larger): 32, which keeps double-buffered records within
+    // shared memory and gives more CTAs work.  Launch class by size.
+    const int per = (cnt[p] >= 4096 && m <= 30) ? 128 : 32;
+    const int pcls = m <= 30 ? 0 : (m <= 48 ? 1 : 2);
+    std::vector<std::pair<int32_t, int32_t>> v;   // (node, slot * 128 + cell)
     for (int64_t c0 = 0; c0 < cnt[p]; c0 += per) {
       const int nc = (int)std::min<int64_t>(per, cnt[p] - c0);
       v.clear();
       for (int k = 0; k < np; ++k)
-        for (int c = 0; c < nc; ++c) {
-          const int64_t pos = (int64_t)k * cnt[p] + c0 + c;
-          v.emplace_back(conn[conn_off[p] + pos], (int32_t)pos);
-        }
+        for (int c = 0; c < nc; ++c)
+          v.emplace_back(conn[conn_off[p] + (int64_t)k * cnt[p] + c0 + c], k * 128 + c);
       std::sort(v.begin(), v.end());
-      TcTile t;
-      t.pat = p;
-      t.ncell = nc;
-      t.cell0 = c0;
-      t.node_off = (int64_t)nodes.size();
-      int cntu = 0;
+      std::vector<int32_t> nodes;
+      std::vector<uint16_t> offs, inc;
       for (size_t i = 0; i < v.size(); ++i) {
         if (i == 0 || v[i].first != v[i - 1].first) {
           nodes.push_back(v[i].first);
-          ++cntu;
+          offs.push_back((uint16_t)inc.size());
         }
-        if (cntu - 1 > 65535) {
-          err = "tile has more than 65536 unique nodes";
-          return SBX_EINVAL;
-        }
-        lidx[conn_off[p] + v[i].second] = (uint16_t)(cntu - 1);
+        const int k = v[i].second / 128, c = v[i].second % 128;
+        inc.push_back((uint16_t)((c << 5) | k));
       }
-      t.n_nodes = cntu;
-      t.pad = 0;
-      const uint32_t need = layout(tp.kpad, tp.npad, cntu, np).total;
-      int cls = 0;
+      offs.push_back((uint16_t)inc.size());
+      const int nn = (int)nodes.size();
+      const RecLayout R = rec_layout(nc, nn, np);
+      const size_t at = recs.size();
+      recs.resize(at + R.bytes, 0);
+      const int32_t hdr[4] = {p, nc, nn, np};
+      put(recs, at, hdr, 4);
+      std::vector<float> sc(nc);
+      for (int c = 0; c < nc; ++c) {
+        recs[at + R.sym + c] = sym_sorted[start[p] + c0 + c];
+        sc[c] = (float)scale_sorted[start[p] + c0 + c];
+      }
+      put(recs, at + R.scale, sc.data(), nc);
+      put(recs, at + R.nodes, nodes.data(), nn);
+      put(recs, at + R.off, offs.data(), offs.size());
+      put(recs, at + R.inc, inc.data(), inc.size());
+      TcTile t;
+      t.rec_off = (int64_t)at;
+      t.rec_bytes = (int32_t)R.bytes;
+      t.pat = p;
+      const uint32_t need = smem_layout(tp.kpad, tp.npad, R.bytes, nn).total;
+      int cls = pcls;
       while (cls < TC_CLASSES - 1 && need > class_limit[cls]) ++cls;
       if (need > class_limit[TC_CLASSES - 1]) {
         err = "tensor-core tile needs more than 227 KB of shared memory";
@@ -318,8 +483,9 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
       }
       kmax[cls] = std::max(kmax[cls], tp.kpad);
       nmax[cls] = std::max(nmax[cls], tp.npad);
-      maxnc[cls] = std::max(maxnc[cls], np);
-      maxn[cls] = std::max(maxn[cls], cntu);
+      recmax[cls] = std::max(recmax[cls], (int)R.bytes);
+      nnmax[cls] = std::max(nnmax[cls], nn);
+      tcols[cls] = std::max(tcols[cls], tp.tcols);
       tiles[cls].push_back(t);
     }
   }
@@ -343,20 +509,24 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   };
   if (int rc = up(&ctx->d_tc_pat, pats)) return rc;
   if (int rc = up(&ctx->d_tc_K, Kc)) return rc;
-  if (int rc = up(&ctx->d_tc_lidx, lidx)) return rc;
-  if (int rc = up(&ctx->d_tc_nodes, nodes)) return rc;
+  if (int rc = up(&ctx->d_tc_rec, recs)) return rc;
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
   for (int cls = 0; cls < TC_CLASSES; ++cls) {
     if (int rc = up(&ctx->d_tc_tiles[cls], tiles[cls])) return rc;
     ctx->n_tc_tiles[cls] = (int)tiles[cls].size();
     ctx->tc_kmax[cls] = kmax[cls];
     ctx->tc_nmax[cls] = nmax[cls];
-    ctx->tc_maxnodes[cls] = maxn[cls];
-    ctx->tc_maxnc[cls] = maxnc[cls];
-    ctx->tc_smem[cls] = layout(kmax[cls], nmax[cls], maxn[cls], maxnc[cls]).total;
-    if (ctx->n_tc_tiles[cls] && ctx->tc_smem[cls] > 227 * 1024) {
-      err = "tensor-core tile needs more than 227 KB of shared memory";
-      return SBX_EINVAL;
-    }
+    ctx->tc_rec_max[cls] = recmax[cls];
+    ctx->tc_nn_max[cls] = nnmax[cls];
+    ctx->tc_tcols[cls] = tcols[cls];
+    const uint32_t smem = smem_layout(kmax[cls], nmax[cls], recmax[cls], nnmax[cls]).total;
+    ctx->tc_smem[cls] = smem;
+    // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per
+    // CTA) and tensor memory (512 columns)
+    int per_sm = (int)((228u * 1024u) / (smem + 1024u));
+    per_sm = std::max(1, std::min(per_sm, std::min(8, 512 / tcols[cls])));
+    ctx->tc_grid[cls] = (int)std::min<int64_t>(tiles[cls].size(), (int64_t)nsm * per_sm);
   }
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     err = "stream synchronisation failed";
@@ -366,7 +536,11 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
 }
 
 cudaError_t prepare_tc_kernels() {
-  return cudaFuncSetAttribute(k_force_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_force_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_force_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              cudaSharedmemCarveoutMaxShared);
 }
 
 cudaError_t launch_force_tc(const sbx_ctx *ctx, const double *u, double *f, double dt,
@@ -377,10 +551,10 @@ cudaError_t launch_force_tc(const sbx_ctx *ctx, const double *u, double *f, doub
     LoadTable L = ctx->loads();
     if (load_done) L.n = 0;
     load_done = true;
-    k_force_tc<<<ctx->n_tc_tiles[cls], 256, ctx->tc_smem[cls], s>>>(
-        ctx->d_tc_tiles[cls], ctx->d_tc_pat, ctx->d_tc_nodes, ctx->d_tc_lidx, ctx->d_tc_K,
-        ctx->d_sym, ctx->d_scale, u, f, L, ctx->d_step, dt, ctx->d_flags,
-        ctx->tc_kmax[cls], ctx->tc_nmax[cls], ctx->tc_maxnodes[cls], ctx->tc_maxnc[cls]);
+    k_force_tc<<<ctx->tc_grid[cls], TC_THREADS, ctx->tc_smem[cls], s>>>(
+        ctx->d_tc_tiles[cls], ctx->n_tc_tiles[cls], ctx->d_tc_rec, ctx->d_tc_pat, ctx->d_tc_K, u,
+        f, L, ctx->d_step, dt, ctx->d_flags, ctx->tc_kmax[cls], ctx->tc_nmax[cls],
+        ctx->tc_rec_max[cls], ctx->tc_nn_max[cls], ctx->tc_tcols[cls]);
   }
   return cudaGetLastError();
 }

@@ -108,10 +108,12 @@ void free_mesh(sbx_ctx *ctx) {
   drop_graph(ctx);
   dfree(ctx->d_conn); dfree(ctx->d_conn_off); dfree(ctx->d_pat_cstart); dfree(ctx->d_pat_ccount);
   dfree(ctx->d_sym); dfree(ctx->d_scale); dfree(ctx->d_minv); dfree(ctx->d_mass);
+  dfree(ctx->d_w);
+  ctx->w_valid = false;
   dfree(ctx->d_u[0]); dfree(ctx->d_u[1]); dfree(ctx->d_f); dfree(ctx->d_tiles_simt);
   dfree(ctx->d_load_dof); dfree(ctx->d_load_amp); dfree(ctx->d_load_t1); dfree(ctx->d_load_ncyc);
   dfree(ctx->d_load_kind);
-  dfree(ctx->d_tc_pat); dfree(ctx->d_tc_K); dfree(ctx->d_tc_lidx); dfree(ctx->d_tc_nodes);
+  dfree(ctx->d_tc_pat); dfree(ctx->d_tc_K); dfree(ctx->d_tc_rec);
   for (int c = 0; c < sbx::TC_CLASSES; ++c) {
     dfree(ctx->d_tc_tiles[c]);
     ctx->n_tc_tiles[c] = 0;
@@ -408,13 +410,14 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   if (!rc) rc = dalloc(ctx, &ctx->d_u[0], ndof);
   if (!rc) rc = dalloc(ctx, &ctx->d_u[1], ndof);
   if (!rc) rc = dalloc(ctx, &ctx->d_f, ndof);
+  if (!rc) rc = dalloc(ctx, &ctx->d_w, ndof);
   if (rc) {
     free_mesh(ctx);
     return rc;
   }
   if (precision_mode == SBX_PREC_MIXED) {
     std::string e;
-    const int trc = sbx::tc_setup(ctx, conn, conn_off, cnt, start, e);
+    const int trc = sbx::tc_setup(ctx, conn, conn_off, cnt, start, ssym, scale, e);
     if (trc) {
       free_mesh(ctx);
       return fail(ctx, trc, e);
@@ -546,6 +549,7 @@ int step_n(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha) {
     CK(cudaMemsetAsync(ctx->d_f, 0, bytes, ctx->stream));
     ctx->f_dirty = false;
   }
+  CK(sbx::prepare_update(ctx, dt, alpha, ctx->stream));
   int64_t left = n_steps - 1;  // the last step keeps R_int for read-back
   if (left >= GRAPH_UNIT) {
     if (!ctx->graph.valid || ctx->graph.dt != dt || ctx->graph.alpha != alpha)
@@ -579,6 +583,7 @@ int sbx_profile(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha, double *
     CK(cudaMemsetAsync(ctx->d_f, 0, bytes, ctx->stream));
     ctx->f_dirty = false;
   }
+  CK(sbx::prepare_update(ctx, dt, alpha, ctx->stream));
   std::vector<cudaEvent_t> ev(3 * n_steps, nullptr);
   int rc = SBX_OK;
   for (auto &e : ev)
@@ -614,6 +619,28 @@ int sbx_profile(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha, double *
   *ms_update = tu;
   if (rc) return rc;
   return check_flags(ctx);
+}
+
+int sbx_query(sbx_ctx *ctx, int what, int64_t *out) {
+  if (!ctx || !out) return SBX_EINVAL;
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
+  int64_t launches = 0, tiles = 0;
+  if (ctx->prec == SBX_PREC_MIXED) {
+    for (int c = 0; c < sbx::TC_CLASSES; ++c) {
+      launches += ctx->n_tc_tiles[c] > 0;
+      tiles += ctx->n_tc_tiles[c];
+    }
+  } else {
+    launches = ctx->n_tiles_simt > 0;
+    tiles = ctx->n_tiles_simt;
+  }
+  switch (what) {
+    case SBX_Q_KERNELS_PER_STEP: *out = launches + 1; break;
+    case SBX_Q_FORCE_LAUNCHES: *out = launches; break;
+    case SBX_Q_TILES: *out = tiles; break;
+    default: return fail(ctx, SBX_EINVAL, "unknown query");
+  }
+  return SBX_OK;
 }
 
 int sbx_get_step(sbx_ctx *ctx, int64_t *n_out) {

@@ -46,13 +46,12 @@ constexpr int TC_CLASSES = 3;
 
 // Tensor-core path: a tile of up to 128 cells of one pattern and its unique
 // nodes (tile_nodes[node_off .. node_off + n_nodes)).
+// A tile's record: one contiguous, 16-byte-padded block in global memory,
+// fetched with one bulk copy (see kernels_tc.cu for its layout).
 struct TcTile {
+  int64_t rec_off;    // byte offset of the record
+  int32_t rec_bytes;  // multiple of 16
   int32_t pat;
-  int32_t ncell;
-  int64_t cell0;      // first cell inside the pattern group
-  int64_t node_off;
-  int32_t n_nodes;
-  int32_t pad;
 };
 struct TcPattern {
   int32_t m, kpad, npad, tcols;  // DOFs, K and N padded for the MMA, TMEM columns
@@ -98,6 +97,9 @@ struct sbx_ctx {
   double *d_scale = nullptr;
   double *d_minv = nullptr;        // 1 / M_diag, 0 on fixed DOFs ([3N])
   double *d_mass = nullptr;        // M_diag ([3N])
+  double *d_w = nullptr;           // dt^2 M^-1 / (1 + alpha dt / 2) for (w_dt, w_alpha)
+  bool w_valid = false;
+  double w_dt = 0.0, w_alpha = 0.0;
   double *d_u[2] = {nullptr, nullptr};
   int cur = 0;                     // d_u[cur] = U_n, d_u[cur ^ 1] = U_{n-1}
   double *d_f = nullptr;           // R_int - R_ext accumulator
@@ -113,12 +115,12 @@ struct sbx_ctx {
   // shared memory they need
   sbx::TcPattern *d_tc_pat = nullptr;
   float *d_tc_K = nullptr;
-  uint16_t *d_tc_lidx = nullptr;
-  int32_t *d_tc_nodes = nullptr;
+  uint8_t *d_tc_rec = nullptr;     // tile records
   sbx::TcTile *d_tc_tiles[sbx::TC_CLASSES] = {};
   int n_tc_tiles[sbx::TC_CLASSES] = {};
-  int tc_kmax[sbx::TC_CLASSES] = {}, tc_nmax[sbx::TC_CLASSES] = {};
-  int tc_maxnodes[sbx::TC_CLASSES] = {}, tc_maxnc[sbx::TC_CLASSES] = {};
+  int tc_kmax[sbx::TC_CLASSES] = {}, tc_nmax[sbx::TC_CLASSES] = {}, tc_tcols[sbx::TC_CLASSES] = {};
+  int tc_rec_max[sbx::TC_CLASSES] = {}, tc_nn_max[sbx::TC_CLASSES] = {};
+  int tc_grid[sbx::TC_CLASSES] = {};
   size_t tc_smem[sbx::TC_CLASSES] = {};
 
   // loads
@@ -143,6 +145,9 @@ namespace sbx {
 constexpr int SIMT_TILE = 32;
 cudaError_t launch_force_simt(const sbx_ctx *ctx, const double *u, double *f, double dt,
                               cudaStream_t s);
+// w = dt^2 M^-1 / (1 + alpha dt / 2) for the update; recomputed when dt or
+// alpha change (outside stream capture).
+cudaError_t prepare_update(sbx_ctx *ctx, double dt, double alpha, cudaStream_t s);
 cudaError_t launch_update(const sbx_ctx *ctx, const double *uc, double *up, double *f, double dt,
                           double alpha, int zero_f, cudaStream_t s);
 cudaError_t launch_init_um1(const sbx_ctx *ctx, const double *u0, const double *v0, double *um1,
@@ -153,7 +158,9 @@ cudaError_t launch_zero_fixed(const sbx_ctx *ctx, double *u, cudaStream_t s);
 cudaError_t prepare_kernels();
 // kernels_tc.cu
 int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<int64_t> &conn_off,
-             const std::vector<int64_t> &cnt, const std::vector<int64_t> &start, std::string &err);
+             const std::vector<int64_t> &cnt, const std::vector<int64_t> &start,
+             const std::vector<uint8_t> &sym_sorted, const std::vector<double> &scale_sorted,
+             std::string &err);
 cudaError_t prepare_tc_kernels();
 cudaError_t launch_force_tc(const sbx_ctx *ctx, const double *u, double *f, double dt,
                             cudaStream_t s);
