@@ -3,7 +3,7 @@
 //
 // Work unit: a tile of up to 128 cells of one pattern p (m = 3 n_p DOFs) and
 // the tile's unique nodes.  The host packs each tile into one contiguous
-// record (layout below) that replaces the connectivity.  Each CTA (128
+// record (layout below) that replaces the connectivity.  Each CTA (256
 // threads) walks tiles blockIdx.x, +gridDim.x, ... with two stages:
 //   * the record of tile i+2 streams in by one 1-D bulk copy (TMA engine,
 //     completion on an mbarrier) and the displacements of tile i+1's nodes by
@@ -22,7 +22,8 @@
 // group (LBO = 128 B, SBO = nK * 128 B).
 //
 // Record layout (every part padded to 16 bytes):
-//   int32 {pat, ncell, nn, n}          header (16 B)
+//   int32 {pat, ncell, nn, n | ident << 16}  header (16 B); ident: every
+//                                      cell of the tile has the identity op
 //   uint8 sym[ncell]                   op of each cell
 //   float scale[ncell]                 E_e h_e rounded to FP32
 //   int32 nodes[nn]                    unique node ids, ascending
@@ -43,7 +44,7 @@ namespace sbx {
 
 namespace {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;
 constexpr uint32_t WAIT_POLLS = 1u << 22;
 
 __host__ __device__ inline uint32_t a16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -93,7 +94,7 @@ struct Stage {
 __device__ inline Stage stage_view(unsigned char *base, uint32_t u_off) {
   Stage S;
   S.hdr = reinterpret_cast<const int32_t *>(base);
-  const RecLayout R = rec_layout(S.hdr[1], S.hdr[2], S.hdr[3]);
+  const RecLayout R = rec_layout(S.hdr[1], S.hdr[2], S.hdr[3] & 0xFFFF);
   S.sym = base + R.sym;
   S.scale = reinterpret_cast<const float *>(base + R.scale);
   S.nodes = reinterpret_cast<const int32_t *>(base + R.nodes);
@@ -101,6 +102,66 @@ __device__ inline Stage stage_view(unsigned char *base, uint32_t u_off) {
   S.inc = reinterpret_cast<const uint16_t *>(base + R.inc);
   S.u = reinterpret_cast<double *>(base + u_off);
   return S;
+}
+
+// One item of A: cell c, nodes 4 k4 .. 4 k4 + 3 (12 columns, three float4
+// per operand).  d = (hi - hi_ref) + (lo - lo_ref) in FP32 with the cell's
+// slot-0 node as reference, transformed by the op, split into TF32 hi + lo.
+// A(c, col) -> float (c/8)*nK*32 + (c%8)*4 + (col/4)*32 + col%4.
+template <bool IDENT>
+__device__ __forceinline__ void build_a_item(int c, int k4, int op, const float *uf,
+                                             const uint16_t *lid, int n, int nK, int kpad,
+                                             float *Ahi, float *Alo) {
+  int p0 = 0, p1 = 1, p2 = 2;
+  float s0 = 1.0f, s1 = 1.0f, s2 = 1.0f;
+  if (!IDENT) {
+    p0 = op_perm_of(op, 0);
+    p1 = op_perm_of(op, 1);
+    p2 = op_perm_of(op, 2);
+    s0 = (op & 1) ? -1.0f : 1.0f;
+    s1 = (op & 2) ? -1.0f : 1.0f;
+    s2 = (op & 4) ? -1.0f : 1.0f;
+  }
+  const float *rf = uf + 6 * lid[c];
+  const float rh[3] = {rf[0], rf[1], rf[2]}, rl[3] = {rf[3], rf[4], rf[5]};
+  const int rowoff = (c >> 3) * nK * 32 + (c & 7) * 4;
+  float vh[12], vl[12];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int k = 4 * k4 + t;
+    float d[3] = {0.0f, 0.0f, 0.0f};
+    if (k < n) {
+      const float *nf = uf + 6 * lid[k * 128 + c];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) d[a] = (nf[a] - rh[a]) + (nf[3 + a] - rl[a]);
+    }
+    float x[3];
+    if (IDENT) {
+      x[0] = d[0];
+      x[1] = d[1];
+      x[2] = d[2];
+    } else {
+      x[0] = s0 * (p0 == 0 ? d[0] : (p0 == 1 ? d[1] : d[2]));
+      x[1] = s1 * (p1 == 0 ? d[0] : (p1 == 1 ? d[1] : d[2]));
+      x[2] = s2 * (p2 == 0 ? d[0] : (p2 == 1 ? d[1] : d[2]));
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      vh[3 * t + r] = tc::to_tf32(x[r]);
+      vl[3 * t + r] = tc::to_tf32(x[r] - vh[3 * t + r]);
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const int q4 = 3 * k4 + g;   // float4 column group
+    if (4 * q4 < kpad) {
+      const int o = rowoff + q4 * 32;
+      *reinterpret_cast<float4 *>(Ahi + o) =
+          make_float4(vh[4 * g], vh[4 * g + 1], vh[4 * g + 2], vh[4 * g + 3]);
+      *reinterpret_cast<float4 *>(Alo + o) =
+          make_float4(vl[4 * g], vl[4 * g + 1], vl[4 * g + 2], vl[4 * g + 3]);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 4)
@@ -232,47 +293,16 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
     // nodes = 12 columns = three float4 stores per operand.
     float *Ahi = As, *Alo = As + 128 * kpad;
     const int nk4 = (kpad + 11) / 12;   // groups of four nodes (12 columns)
-    for (int w = tid; w < ncell * nk4; w += TC_THREADS) {
-      const int c = w % ncell, k4 = w / ncell;
-      const int op = S.sym[c];
-      const int p0 = op_perm_of(op, 0), p1 = op_perm_of(op, 1), p2 = op_perm_of(op, 2);
-      const float s0 = (op & 1) ? -1.0f : 1.0f, s1 = (op & 2) ? -1.0f : 1.0f,
-                  s2 = (op & 4) ? -1.0f : 1.0f;
+    const bool ident = ((S.hdr[3] >> 16) & 1) != 0;   // every cell has the identity op
+    {
       const float *uf = reinterpret_cast<const float *>(S.u);
-      const float *rf = uf + 6 * lid[c];
-      const float rh[3] = {rf[0], rf[1], rf[2]}, rl[3] = {rf[3], rf[4], rf[5]};
-      const int rowoff = (c >> 3) * nK * 32 + (c & 7) * 4;
-      {
-        float vh[12], vl[12];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int k = 4 * k4 + t;
-          float d[3] = {0.0f, 0.0f, 0.0f};
-          if (k < n) {
-            const float *nf = uf + 6 * lid[k * 128 + c];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) d[a] = (nf[a] - rh[a]) + (nf[3 + a] - rl[a]);
-          }
-          const float x[3] = {s0 * (p0 == 0 ? d[0] : (p0 == 1 ? d[1] : d[2])),
-                              s1 * (p1 == 0 ? d[0] : (p1 == 1 ? d[1] : d[2])),
-                              s2 * (p2 == 0 ? d[0] : (p2 == 1 ? d[1] : d[2]))};
-#pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            vh[3 * t + r] = tc::to_tf32(x[r]);
-            vl[3 * t + r] = tc::to_tf32(x[r] - vh[3 * t + r]);
-          }
-        }
-#pragma unroll
-        for (int g = 0; g < 3; ++g) {
-          const int q4 = 3 * k4 + g;            // float4 column group
-          if (4 * q4 < kpad) {
-            const int o = rowoff + q4 * 32;
-            *reinterpret_cast<float4 *>(Ahi + o) =
-                make_float4(vh[4 * g], vh[4 * g + 1], vh[4 * g + 2], vh[4 * g + 3]);
-            *reinterpret_cast<float4 *>(Alo + o) =
-                make_float4(vl[4 * g], vl[4 * g + 1], vl[4 * g + 2], vl[4 * g + 3]);
-          }
-        }
+      if (ident) {
+        for (int w = tid; w < ncell * nk4; w += TC_THREADS)
+          build_a_item<true>(w % ncell, w / ncell, 0, uf, lid, n, nK, kpad, Ahi, Alo);
+      } else {
+        for (int w = tid; w < ncell * nk4; w += TC_THREADS)
+          build_a_item<false>(w % ncell, w / ncell, S.sym[w % ncell], uf, lid, n, nK, kpad, Ahi,
+                              Alo);
       }
     }
     tc::fence_proxy_async_smem();
@@ -298,14 +328,17 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
     tc::fence_after_sync();
     if (!ok) break;
     ph_mma ^= 1u;
-    // epilogue: warp w holds TMEM lanes 32w..32w+31 (cells); F = E h D
-    // (FP32, row stride npad + 1) overwrites A
+    // epilogue: warps w and w + 4 hold TMEM lanes 32 (w % 4) .. + 31 (cells)
+    // and split the columns; F = E h D (FP32, row stride npad + 1)
+    // overwrites A
     float *F = As;
     {
-      const int c = 32 * warp + lane;
+      const int c = 32 * (warp & 3) + lane;
       const float sc = c < ncell ? S.scale[c] : 0.0f;
-      const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-      for (int cc = 0; cc < npad; cc += 8) {
+      const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+      const int half = npad / 2;                // a multiple of 8
+      const int c0 = (warp >> 2) * half;
+      for (int cc = c0; cc < c0 + half; cc += 8) {
         float v[8];
         tc::tmem_ld8(taddr + lane_base + (uint32_t)cc, v);
         tc::tmem_ld_wait();
@@ -315,8 +348,13 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
             if (cc + q < m) F[c * (npad + 1) + cc + q] = sc * v[q];
         }
       }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    {
+      const int c = tid;
       // back to the cell frame, node by node: f_cell[perm r] = sign_r f_master[r]
-      if (c < ncell) {
+      if (c < ncell && !ident) {
         const int op = S.sym[c];
         const int p0 = op_perm_of(op, 0), p1 = op_perm_of(op, 1), p2 = op_perm_of(op, 2);
         float *Fr = F + c * (npad + 1);
@@ -459,13 +497,15 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
       const RecLayout R = rec_layout(nc, nn, np);
       const size_t at = recs.size();
       recs.resize(at + R.bytes, 0);
-      const int32_t hdr[4] = {p, nc, nn, np};
-      put(recs, at, hdr, 4);
       std::vector<float> sc(nc);
+      int ident = 1;
       for (int c = 0; c < nc; ++c) {
         recs[at + R.sym + c] = sym_sorted[start[p] + c0 + c];
+        ident &= sym_sorted[start[p] + c0 + c] == 0;
         sc[c] = (float)scale_sorted[start[p] + c0 + c];
       }
+      const int32_t hdr[4] = {p, nc, nn, np | (ident << 16)};   // bit 16: all ops identity
+      put(recs, at, hdr, 4);
       put(recs, at + R.scale, sc.data(), nc);
       put(recs, at + R.nodes, nodes.data(), nn);
       put(recs, at + R.off, offs.data(), offs.size());
