@@ -1,0 +1,358 @@
+// Batched explicit step: B load cases advance together (field layout
+// [node][3][B], entry (3 node + d) B + b).  K_p is read once per cell and
+// applied to the 32 load cases of a chunk, so the contraction is a small
+// dense GEMM per cell (K_p times an m x 32 block).
+//
+// Force kernel, one CTA (8 warps) per (tile of cells of one pattern, chunk
+// of 32 load cases); lane = load case:
+//   1. gather the tile's unique nodes (the 32 cases of each DOF form one
+//      coalesced 256-byte row); T = float: split each value into FP32 hi + lo
+//      once (bit operations), T = double: keep FP64;
+//   2. warp per cell: for j = 0..m-1, d_j = U(node) - U(slot-0 node) of this
+//      lane's case (K_p annihilates translations), transformed by the op
+//      (Sec. 3.2.2); acc(0..MM) += K_p(j, :) d_j with K_p rows read as float4
+//      broadcasts (K_p is symmetric, so row j is column j);
+//   3. E_e h_e Q^T acc is added into a per-tile accumulator in shared memory,
+//      then one coalesced FP64 atomic per (node, DOF, case) into f.
+// T = float: FP32 contraction; T = double: FP64.  The update is FP64.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <vector>
+
+#include "device_common.cuh"
+#include "sbx_internal.cuh"
+
+namespace sbx {
+namespace {
+
+constexpr int BT_THREADS = 256;   // 8 warps
+constexpr int BT_WARPS = 8;
+constexpr int BC = 32;            // load cases per chunk
+constexpr uint32_t BT_SMEM_TARGET = 100u * 1024u;   // two CTAs per SM
+
+__host__ __device__ inline uint32_t b16(uint32_t x) { return (x + 15u) & ~15u; }
+
+// Record: int32 {pat, ncell, nn, n}; uint8 sym[ncell]; double scale[ncell];
+// int32 nodes[nn]; uint16 lid[n][ncell] (local node of slot k of cell c)
+struct BRecLayout {
+  uint32_t sym, scale, nodes, lid, bytes;
+};
+__host__ __device__ inline BRecLayout brec_layout(int ncell, int nn, int n) {
+  BRecLayout R;
+  uint32_t o = 16;
+  R.sym = o;   o += b16((uint32_t)ncell);
+  R.scale = o; o += b16(8u * ncell);
+  R.nodes = o; o += b16(4u * nn);
+  R.lid = o;   o += b16(2u * n * ncell);
+  R.bytes = o;
+  return R;
+}
+
+struct BSmem {
+  uint32_t K, u, f, rec, total;
+};
+// mm: padded row length of K_p (a multiple of 4); tsz: sizeof(T)
+__host__ __device__ inline BSmem bsmem(int mm, int nn_max, int rec_max, uint32_t tsz) {
+  BSmem L;
+  uint32_t o = 0;
+  L.K = o;   o = b16(o + (uint32_t)mm * mm * tsz);
+  L.u = o;   o = b16(o + (uint32_t)nn_max * 3u * BC * 8u);          // float2 or double
+  L.f = o;   o = b16(o + (uint32_t)nn_max * 3u * BC * tsz);
+  L.rec = o; o = b16(o + (uint32_t)rec_max);
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ double to_f64(float x) { return f2d_bits(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+
+template <typename T, int MM>
+__global__ void __launch_bounds__(BT_THREADS, 2)
+    k_force_batch(const TcTile *__restrict__ tiles, int nchunks, const uint8_t *__restrict__ recs,
+                  const T *__restrict__ Kp, const int64_t *__restrict__ koff,
+                  const double *__restrict__ u, double *__restrict__ f, int B, LoadTable Ld,
+                  const int64_t *__restrict__ d_step, double dt, int nn_max, int rec_max) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BSmem SL = bsmem(MM, nn_max, rec_max, sizeof(T));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x / nchunks, chunk = blockIdx.x % nchunks;
+  const TcTile Tt = tiles[tile];
+  {
+    const int4 *src = reinterpret_cast<const int4 *>(recs + Tt.rec_off);
+    int4 *dst = reinterpret_cast<int4 *>(smem + SL.rec);
+    for (int q = tid; q < Tt.rec_bytes / 16; q += BT_THREADS) dst[q] = src[q];
+  }
+  __syncthreads();
+  const int32_t *hdr = reinterpret_cast<const int32_t *>(smem + SL.rec);
+  const int pat = hdr[0], ncell = hdr[1], nn = hdr[2], n = hdr[3];
+  const int m = 3 * n;
+  const BRecLayout R = brec_layout(ncell, nn, n);
+  const uint8_t *sym = smem + SL.rec + R.sym;
+  const double *scale = reinterpret_cast<const double *>(smem + SL.rec + R.scale);
+  const int32_t *nodes = reinterpret_cast<const int32_t *>(smem + SL.rec + R.nodes);
+  const uint16_t *lid = reinterpret_cast<const uint16_t *>(smem + SL.rec + R.lid);
+  T *Ks = reinterpret_cast<T *>(smem + SL.K);
+  T *fs = reinterpret_cast<T *>(smem + SL.f);
+
+  // K_p, rows padded to MM with zeros (symmetric: row j = column j)
+  for (int q = tid; q < m * MM; q += BT_THREADS) {
+    const int j = q / MM, i = q % MM;
+    Ks[q] = i < m ? (T)Kp[koff[pat] + (int64_t)j * m + i] : (T)0;
+  }
+  const int b0 = chunk * BC;
+  for (int q = tid; q < nn * 3 * BC; q += BT_THREADS) {
+    const int nq = q / (3 * BC), a = (q / BC) % 3, b = q % BC;
+    const double x = u[(3 * (int64_t)nodes[nq] + a) * B + b0 + b];
+    if constexpr (sizeof(T) == 4) {
+      float hi, lo;
+      split_f64(x, hi, lo);
+      reinterpret_cast<float2 *>(smem + SL.u)[q] = make_float2(hi, lo);
+    } else {
+      reinterpret_cast<double *>(smem + SL.u)[q] = x;
+    }
+    fs[q] = (T)0;
+  }
+  __syncthreads();
+
+  for (int c = warp; c < ncell; c += BT_WARPS) {
+    const int op = sym[c];
+    const int p0 = op_perm_of(op, 0), p1 = op_perm_of(op, 1), p2 = op_perm_of(op, 2);
+    const int q0 = lid[c];
+    T acc[MM];
+#pragma unroll
+    for (int i = 0; i < MM; ++i) acc[i] = (T)0;
+    for (int j = 0; j < m; ++j) {
+      const int k = j / 3, r = j - 3 * (j / 3);
+      const int a = r == 0 ? p0 : (r == 1 ? p1 : p2);
+      const int q = lid[k * ncell + c];
+      T d;
+      if constexpr (sizeof(T) == 4) {
+        const float2 *uu = reinterpret_cast<const float2 *>(smem + SL.u);
+        const float2 v = uu[(q * 3 + a) * BC + lane], v0 = uu[(q0 * 3 + a) * BC + lane];
+        d = (v.x - v0.x) + (v.y - v0.y);
+      } else {
+        const double *uu = reinterpret_cast<const double *>(smem + SL.u);
+        d = uu[(q * 3 + a) * BC + lane] - uu[(q0 * 3 + a) * BC + lane];
+      }
+      if ((op >> r) & 1) d = -d;
+      const T *kr = Ks + j * MM;
+#pragma unroll
+      for (int i = 0; i < MM; i += 4) {
+        if constexpr (sizeof(T) == 4) {
+          const float4 kv = *reinterpret_cast<const float4 *>(kr + i);
+          acc[i] += kv.x * d;
+          acc[i + 1] += kv.y * d;
+          acc[i + 2] += kv.z * d;
+          acc[i + 3] += kv.w * d;
+        } else {
+          acc[i] += kr[i] * d;
+          acc[i + 1] += kr[i + 1] * d;
+          acc[i + 2] += kr[i + 2] * d;
+          acc[i + 3] += kr[i + 3] * d;
+        }
+      }
+    }
+    const T s = (T)scale[c];
+#pragma unroll
+    for (int i = 0; i < MM; ++i) {
+      if (i < m) {
+        const int k = i / 3, r = i % 3;
+        const int a = r == 0 ? p0 : (r == 1 ? p1 : p2);
+        const T v = ((op >> r) & 1) ? -s * acc[i] : s * acc[i];
+        atomicAdd(&fs[(lid[k * ncell + c] * 3 + a) * BC + lane], v);
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < nn * 3 * BC; q += BT_THREADS) {
+    const int nq = q / (3 * BC), a = (q / BC) % 3, b = q % BC;
+    atomicAdd(&f[(3 * (int64_t)nodes[nq] + a) * B + b0 + b], to_f64(fs[q]));
+  }
+  if (blockIdx.x == 0 && Ld.n > 0) {
+    const double t = (double)(*d_step) * dt;
+    for (int l = tid; l < Ld.n; l += BT_THREADS)
+      atomicAdd(&f[Ld.dof[l]], -Ld.amp[l] * wavelet_value(Ld.kind[l], t, Ld.t1[l], Ld.ncyc[l]));
+  }
+}
+
+// U_{n+1} = -w f + 2 U_n - U_{n-1} (undamped) or the damped form; w per DOF,
+// f and U per (DOF, case); FP64.
+template <bool DAMPED>
+__global__ void __launch_bounds__(256)
+    k_update_batch(int64_t nd, int B, const double *__restrict__ w, double *__restrict__ f,
+                   const double *__restrict__ uc, double *__restrict__ up, double a, double b,
+                   int zero_f, int32_t *flags, int64_t *d_step) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double wv = w[i / B];
+    const double r = DAMPED ? fma(-wv, f[i], fma(a, uc[i], -b * up[i]))
+                            : fma(-wv, f[i], fma(2.0, uc[i], -up[i]));
+    bad |= ((__double_as_longlong(r) >> 52) & 0x7FF) == 0x7FF;
+    up[i] = r;
+    if (zero_f) f[i] = 0.0;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *d_step += 1;
+}
+
+int class_of(int m) { return m <= 24 ? 0 : (m <= 48 ? 1 : 2); }
+constexpr int CLASS_MM[3] = {24, 48, 80};
+
+}  // namespace
+
+int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<int64_t> &conn_off,
+                const std::vector<int64_t> &cnt, const std::vector<uint8_t> &sym_sorted,
+                const std::vector<double> &scale_sorted, const std::vector<int64_t> &start,
+                std::string &err) {
+  const int P = ctx->n_pat;
+  const uint32_t tsz = ctx->prec == SBX_PREC_FP64 ? 8u : 4u;
+  std::vector<uint8_t> recs;
+  std::vector<TcTile> tiles[3];
+  int nnmax[3] = {1, 1, 1}, recmax[3] = {16, 16, 16};
+  std::vector<std::pair<int32_t, int32_t>> v;
+  for (int p = 0; p < P; ++p) {
+    const int np = ctx->pat_nodes[p], m = 3 * np, cls = class_of(m);
+    int64_t c0 = 0;
+    while (c0 < cnt[p]) {
+      // largest tile (16 cells or fewer) whose staging fits the target
+      int nc = (int)std::min<int64_t>(16, cnt[p] - c0);
+      std::vector<int32_t> nodes;
+      std::vector<uint16_t> lid;
+      for (;;) {
+        v.clear();
+        for (int k = 0; k < np; ++k)
+          for (int c = 0; c < nc; ++c)
+            v.emplace_back(conn[conn_off[p] + (int64_t)k * cnt[p] + c0 + c], k * nc + c);
+        std::sort(v.begin(), v.end());
+        nodes.clear();
+        lid.assign((size_t)np * nc, 0);
+        for (size_t i = 0; i < v.size(); ++i) {
+          if (i == 0 || v[i].first != v[i - 1].first) nodes.push_back(v[i].first);
+          lid[v[i].second] = (uint16_t)(nodes.size() - 1);
+        }
+        const uint32_t need = bsmem(CLASS_MM[cls], (int)nodes.size(),
+                                    (int)brec_layout(nc, (int)nodes.size(), np).bytes, tsz).total;
+        if (need <= BT_SMEM_TARGET || nc == 1) break;
+        nc = std::max(1, nc / 2);
+      }
+      const int nn = (int)nodes.size();
+      const BRecLayout R = brec_layout(nc, nn, np);
+      const size_t at = recs.size();
+      recs.resize(at + R.bytes, 0);
+      const int32_t hdr[4] = {p, nc, nn, np};
+      memcpy(recs.data() + at, hdr, 16);
+      for (int c = 0; c < nc; ++c) {
+        recs[at + R.sym + c] = sym_sorted[start[p] + c0 + c];
+        memcpy(recs.data() + at + R.scale + 8 * c, &scale_sorted[start[p] + c0 + c], 8);
+      }
+      memcpy(recs.data() + at + R.nodes, nodes.data(), 4 * nn);
+      memcpy(recs.data() + at + R.lid, lid.data(), 2 * lid.size());
+      TcTile t;
+      t.rec_off = (int64_t)at;
+      t.rec_bytes = (int32_t)R.bytes;
+      t.pat = p;
+      tiles[cls].push_back(t);
+      nnmax[cls] = std::max(nnmax[cls], nn);
+      recmax[cls] = std::max(recmax[cls], (int)R.bytes);
+      c0 += nc;
+    }
+  }
+  auto up = [&](auto **dst, const auto &vec) -> int {
+    using TT = typename std::remove_reference<decltype(vec)>::type::value_type;
+    if (*dst) cudaFree(*dst);
+    *dst = nullptr;
+    if (cudaMalloc((void **)dst, std::max<size_t>(vec.size(), 1) * sizeof(TT)) != cudaSuccess) {
+      cudaGetLastError();
+      err = "cudaMalloc failed (batched tables)";
+      return SBX_ENOMEM;
+    }
+    if (!vec.empty() && cudaMemcpyAsync(*dst, vec.data(), vec.size() * sizeof(TT),
+                                        cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+      err = "copy of batched tables failed";
+      return SBX_ECUDA;
+    }
+    return SBX_OK;
+  };
+  if (int rc = up(&ctx->d_b_rec, recs)) return rc;
+  for (int c = 0; c < 3; ++c) {
+    if (int rc = up(&ctx->d_b_tiles[c], tiles[c])) return rc;
+    ctx->n_b_tiles[c] = (int)tiles[c].size();
+    ctx->b_nnmax[c] = nnmax[c];
+    ctx->b_recmax[c] = recmax[c];
+    ctx->b_smem[c] = bsmem(CLASS_MM[c], nnmax[c], recmax[c], tsz).total;
+    if (ctx->n_b_tiles[c] && ctx->b_smem[c] > 227u * 1024u) {
+      err = "batched tile needs more than 227 KB of shared memory";
+      return SBX_EINVAL;
+    }
+  }
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    err = "stream synchronisation failed";
+    return SBX_ECUDA;
+  }
+  return SBX_OK;
+}
+
+cudaError_t prepare_batch_kernels() {
+  const void *ks[6] = {(const void *)k_force_batch<float, 24>, (const void *)k_force_batch<float, 48>,
+                       (const void *)k_force_batch<float, 80>, (const void *)k_force_batch<double, 24>,
+                       (const void *)k_force_batch<double, 48>, (const void *)k_force_batch<double, 80>};
+  for (const void *k : ks) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+static void launch_class(const sbx_ctx *ctx, int c, const T *K, const double *u, double *f,
+                         LoadTable L, double dt, cudaStream_t s) {
+  const int nchunks = ctx->B / BC;
+  const unsigned grid = (unsigned)ctx->n_b_tiles[c] * (unsigned)nchunks;
+  const size_t sm = ctx->b_smem[c];
+#define SBX_LAUNCH(MMV)                                                                        \
+  k_force_batch<T, MMV><<<grid, BT_THREADS, sm, s>>>(ctx->d_b_tiles[c], nchunks, ctx->d_b_rec, \
+                                                     K, ctx->d_koff, u, f, ctx->B, L,          \
+                                                     ctx->d_step, dt, ctx->b_nnmax[c],         \
+                                                     ctx->b_recmax[c])
+  if (c == 0) SBX_LAUNCH(24);
+  else if (c == 1) SBX_LAUNCH(48);
+  else SBX_LAUNCH(80);
+#undef SBX_LAUNCH
+}
+
+cudaError_t launch_force_batch(const sbx_ctx *ctx, const double *u, double *f, double dt,
+                               cudaStream_t s) {
+  bool load_done = false;
+  for (int c = 0; c < 3; ++c) {
+    if (ctx->n_b_tiles[c] == 0) continue;
+    LoadTable L = ctx->loads();
+    if (load_done) L.n = 0;
+    load_done = true;
+    if (ctx->prec == SBX_PREC_FP64)
+      launch_class<double>(ctx, c, ctx->d_K64, u, f, L, dt, s);
+    else
+      launch_class<float>(ctx, c, ctx->d_K32, u, f, L, dt, s);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_batch(const sbx_ctx *ctx, const double *uc, double *up, double *f,
+                                double dt, double alpha, int zero_f, cudaStream_t s) {
+  const int64_t nd = ctx->ndof * ctx->B;
+  const double cm = 1.0 - 0.5 * alpha * dt, cp = 1.0 + 0.5 * alpha * dt;
+  const int64_t want = (nd + 255) / 256;
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), 152 * 8);
+  if (alpha == 0.0)
+    k_update_batch<false><<<grid, 256, 0, s>>>(nd, ctx->B, ctx->d_w, f, uc, up, 2.0, 1.0, zero_f,
+                                               ctx->d_flags, ctx->d_step);
+  else
+    k_update_batch<true><<<grid, 256, 0, s>>>(nd, ctx->B, ctx->d_w, f, uc, up, 2.0 / cp, cm / cp,
+                                              zero_f, ctx->d_flags, ctx->d_step);
+  return cudaGetLastError();
+}
+
+}  // namespace sbx

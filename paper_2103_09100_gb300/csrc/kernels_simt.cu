@@ -237,7 +237,7 @@ __global__ void k_make_w(int64_t nd, const double *minv, double *w, double c) {
 
 cudaError_t prepare_update(sbx_ctx *ctx, double dt, double alpha, cudaStream_t s) {
   if (ctx->w_valid && ctx->w_dt == dt && ctx->w_alpha == alpha) return cudaSuccess;
-  const int64_t nd = ctx->ndof * ctx->B;
+  const int64_t nd = ctx->ndof;   // w is per DOF, shared by all load cases
   const double cp = 1.0 + 0.5 * alpha * dt;
   k_make_w<<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_minv, ctx->d_w, dt * dt / cp);
   cudaError_t e = cudaGetLastError();
@@ -265,16 +265,19 @@ cudaError_t launch_update(const sbx_ctx *ctx, const double *uc, double *up, doub
 // ---------------------------------------------------------------- start-up
 // Eq. (D0): U_-1 = U_0 - dt V_0 + dt^2/2 A_0 with A_0 = -M^-1 f - alpha V_0,
 // f = K U_0 - R_ext(0).  Fixed DOFs (minv == 0) stay zero.
-__global__ void k_init_um1(int64_t nd, const double *minv, const double *u0, const double *v0,
-                           double *um1, const double *f, double dt, double alpha) {
+// Fields hold B load cases per DOF (entry DOF * B + case); minv is per DOF.
+__global__ void k_init_um1(int64_t nd, int B, const double *minv, const double *u0,
+                           const double *v0, double *um1, const double *f, double dt,
+                           double alpha) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double v = v0 ? v0[i] : 0.0;
-    if (minv[i] == 0.0) {
+    const double mi = minv[i / B];
+    if (mi == 0.0) {
       um1[i] = 0.0;
       continue;
     }
-    const double acc = -minv[i] * f[i] - alpha * v;
+    const double acc = -mi * f[i] - alpha * v;
     um1[i] = u0[i] - dt * v + 0.5 * dt * dt * acc;
   }
 }
@@ -282,19 +285,19 @@ __global__ void k_init_um1(int64_t nd, const double *minv, const double *u0, con
 cudaError_t launch_init_um1(const sbx_ctx *ctx, const double *u0, const double *v0, double *um1,
                             const double *f, double dt, double alpha, cudaStream_t s) {
   const int64_t nd = ctx->ndof * ctx->B;
-  k_init_um1<<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_minv, u0, v0, um1, f, dt, alpha);
+  k_init_um1<<<update_grid(nd), 256, 0, s>>>(nd, ctx->B, ctx->d_minv, u0, v0, um1, f, dt, alpha);
   return cudaGetLastError();
 }
 
-__global__ void k_zero_fixed(int64_t nd, const double *minv, double *u) {
+__global__ void k_zero_fixed(int64_t nd, int B, const double *minv, double *u) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd;
        i += (int64_t)gridDim.x * blockDim.x)
-    if (minv[i] == 0.0) u[i] = 0.0;
+    if (minv[i / B] == 0.0) u[i] = 0.0;
 }
 
 cudaError_t launch_zero_fixed(const sbx_ctx *ctx, double *u, cudaStream_t s) {
   const int64_t nd = ctx->ndof * ctx->B;
-  k_zero_fixed<<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_minv, u);
+  k_zero_fixed<<<update_grid(nd), 256, 0, s>>>(nd, ctx->B, ctx->d_minv, u);
   return cudaGetLastError();
 }
 

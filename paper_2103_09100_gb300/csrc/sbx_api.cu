@@ -114,6 +114,11 @@ void free_mesh(sbx_ctx *ctx) {
   dfree(ctx->d_load_dof); dfree(ctx->d_load_amp); dfree(ctx->d_load_t1); dfree(ctx->d_load_ncyc);
   dfree(ctx->d_load_kind);
   dfree(ctx->d_tc_pat); dfree(ctx->d_tc_K); dfree(ctx->d_tc_rec);
+  dfree(ctx->d_b_rec);
+  for (int c = 0; c < 3; ++c) {
+    dfree(ctx->d_b_tiles[c]);
+    ctx->n_b_tiles[c] = 0;
+  }
   for (int c = 0; c < sbx::TC_CLASSES; ++c) {
     dfree(ctx->d_tc_tiles[c]);
     ctx->n_tc_tiles[c] = 0;
@@ -133,10 +138,21 @@ int set_device(sbx_ctx *ctx) {
 }
 
 int force(sbx_ctx *ctx, const double *u, double *f, double dt) {
-  if (ctx->prec == SBX_PREC_MIXED) {
+  if (ctx->B > 1) {
+    CK(sbx::launch_force_batch(ctx, u, f, dt, ctx->stream));
+  } else if (ctx->prec == SBX_PREC_MIXED) {
     CK(sbx::launch_force_tc(ctx, u, f, dt, ctx->stream));
   } else {
     CK(sbx::launch_force_simt(ctx, u, f, dt, ctx->stream));
+  }
+  return SBX_OK;
+}
+
+int update(sbx_ctx *ctx, const double *uc, double *up, double dt, double alpha, int zero_f) {
+  if (ctx->B > 1) {
+    CK(sbx::launch_update_batch(ctx, uc, up, ctx->d_f, dt, alpha, zero_f, ctx->stream));
+  } else {
+    CK(sbx::launch_update(ctx, uc, up, ctx->d_f, dt, alpha, zero_f, ctx->stream));
   }
   return SBX_OK;
 }
@@ -146,8 +162,7 @@ int one_step(sbx_ctx *ctx, int parity, double dt, double alpha, int zero_f) {
   double *uc = ctx->d_u[parity], *up = ctx->d_u[parity ^ 1];
   int rc = force(ctx, uc, ctx->d_f, dt);
   if (rc) return rc;
-  CK(sbx::launch_update(ctx, uc, up, ctx->d_f, dt, alpha, zero_f, ctx->stream));
-  return SBX_OK;
+  return update(ctx, uc, up, dt, alpha, zero_f);
 }
 
 constexpr int GRAPH_UNIT = 32;  // steps per replayed graph (even)
@@ -210,7 +225,8 @@ int sbx_create(sbx_ctx **out, int device, void *cuda_stream) {
     }
     ctx->own_stream = true;
   }
-  if (sbx::prepare_kernels() != cudaSuccess || sbx::prepare_tc_kernels() != cudaSuccess) {
+  if (sbx::prepare_kernels() != cudaSuccess || sbx::prepare_tc_kernels() != cudaSuccess ||
+      sbx::prepare_batch_kernels() != cudaSuccess) {
     cudaGetLastError();
     sbx_destroy(ctx);
     return SBX_ECUDA;
@@ -313,7 +329,10 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   if (ctx->n_pat == 0) return fail(ctx, SBX_ESTATE, "set_patterns must come before mesh_upload");
   if (n_nodes < 1 || n_cells < 1 || n_nodes > (int64_t)INT32_MAX)
     return fail(ctx, SBX_EINVAL, "n_nodes / n_cells out of range");
-  if (n_rhs != 1) return fail(ctx, SBX_EINVAL, "n_rhs > 1 needs the batched build");
+  if (n_rhs != 1 && (n_rhs < 32 || n_rhs % 32 != 0 || n_rhs > 1024))
+    return fail(ctx, SBX_EINVAL, "n_rhs must be 1 or a multiple of 32 up to 1024");
+  if (n_rhs > 1 && precision_mode == SBX_PREC_MIXED)
+    return fail(ctx, SBX_EINVAL, "the batched form runs SBX_PREC_FP32 or SBX_PREC_FP64");
   if (precision_mode != SBX_PREC_FP64 && precision_mode != SBX_PREC_FP32 &&
       precision_mode != SBX_PREC_MIXED)
     return fail(ctx, SBX_EINVAL, "unknown precision_mode");
@@ -407,15 +426,25 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   if (!rc) rc = upload(ctx, &ctx->d_minv, minv);
   if (!rc) rc = upload(ctx, &ctx->d_mass, mass);
   if (!rc) rc = upload(ctx, &ctx->d_tiles_simt, tiles);
-  if (!rc) rc = dalloc(ctx, &ctx->d_u[0], ndof);
-  if (!rc) rc = dalloc(ctx, &ctx->d_u[1], ndof);
-  if (!rc) rc = dalloc(ctx, &ctx->d_f, ndof);
+  const int64_t nfield = ndof * n_rhs;
+  if (!rc) rc = dalloc(ctx, &ctx->d_u[0], nfield);
+  if (!rc) rc = dalloc(ctx, &ctx->d_u[1], nfield);
+  if (!rc) rc = dalloc(ctx, &ctx->d_f, nfield);
   if (!rc) rc = dalloc(ctx, &ctx->d_w, ndof);
   if (rc) {
     free_mesh(ctx);
     return rc;
   }
-  if (precision_mode == SBX_PREC_MIXED) {
+  ctx->prec = precision_mode;
+  ctx->B = n_rhs;
+  if (n_rhs > 1) {
+    std::string e;
+    const int brc = sbx::batch_setup(ctx, conn, conn_off, cnt, ssym, scale, start, e);
+    if (brc) {
+      free_mesh(ctx);
+      return fail(ctx, brc, e);
+    }
+  } else if (precision_mode == SBX_PREC_MIXED) {
     std::string e;
     const int trc = sbx::tc_setup(ctx, conn, conn_off, cnt, start, ssym, scale, e);
     if (trc) {
@@ -423,9 +452,9 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
       return fail(ctx, trc, e);
     }
   }
-  CK(cudaMemsetAsync(ctx->d_u[0], 0, ndof * sizeof(double), ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_u[1], 0, ndof * sizeof(double), ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_f, 0, ndof * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_u[0], 0, nfield * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_u[1], 0, nfield * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_f, 0, nfield * sizeof(double), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(int64_t), ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -593,9 +622,7 @@ int sbx_profile(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha, double *
     cudaEventRecord(ev[3 * s], ctx->stream);
     rc = force(ctx, uc, ctx->d_f, dt);
     cudaEventRecord(ev[3 * s + 1], ctx->stream);
-    if (rc == SBX_OK && sbx::launch_update(ctx, uc, up, ctx->d_f, dt, alpha, s + 1 < n_steps, ctx->stream) !=
-                            cudaSuccess)
-      rc = fail(ctx, SBX_ECUDA, "update launch failed");
+    if (rc == SBX_OK) rc = update(ctx, uc, up, dt, alpha, s + 1 < n_steps);
     cudaEventRecord(ev[3 * s + 2], ctx->stream);
     ctx->cur ^= 1;
     ctx->step += 1;
@@ -625,7 +652,12 @@ int sbx_query(sbx_ctx *ctx, int what, int64_t *out) {
   if (!ctx || !out) return SBX_EINVAL;
   if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
   int64_t launches = 0, tiles = 0;
-  if (ctx->prec == SBX_PREC_MIXED) {
+  if (ctx->B > 1) {
+    for (int c = 0; c < 3; ++c) {
+      launches += ctx->n_b_tiles[c] > 0;
+      tiles += (int64_t)ctx->n_b_tiles[c] * (ctx->B / 32);
+    }
+  } else if (ctx->prec == SBX_PREC_MIXED) {
     for (int c = 0; c < sbx::TC_CLASSES; ++c) {
       launches += ctx->n_tc_tiles[c] > 0;
       tiles += ctx->n_tc_tiles[c];

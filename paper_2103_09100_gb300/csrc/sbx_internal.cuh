@@ -123,6 +123,12 @@ struct sbx_ctx {
   int tc_grid[sbx::TC_CLASSES] = {};
   size_t tc_smem[sbx::TC_CLASSES] = {};
 
+  // batched path (n_rhs > 1): tile records in three classes by pattern size
+  uint8_t *d_b_rec = nullptr;
+  sbx::TcTile *d_b_tiles[3] = {};
+  int n_b_tiles[3] = {}, b_nnmax[3] = {}, b_recmax[3] = {};
+  size_t b_smem[3] = {};
+
   // loads
   int n_load = 0;
   int64_t *d_load_dof = nullptr;
@@ -162,6 +168,16 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
              const std::vector<uint8_t> &sym_sorted, const std::vector<double> &scale_sorted,
              std::string &err);
 cudaError_t prepare_tc_kernels();
+// kernels_batch.cu
+int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<int64_t> &conn_off,
+                const std::vector<int64_t> &cnt, const std::vector<uint8_t> &sym_sorted,
+                const std::vector<double> &scale_sorted, const std::vector<int64_t> &start,
+                std::string &err);
+cudaError_t prepare_batch_kernels();
+cudaError_t launch_force_batch(const sbx_ctx *ctx, const double *u, double *f, double dt,
+                               cudaStream_t s);
+cudaError_t launch_update_batch(const sbx_ctx *ctx, const double *uc, double *up, double *f,
+                                double dt, double alpha, int zero_f, cudaStream_t s);
 cudaError_t launch_force_tc(const sbx_ctx *ctx, const double *u, double *f, double dt,
                             cudaStream_t s);
 }  // namespace sbx
