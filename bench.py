@@ -1,15 +1,25 @@
 """Benchmark: DOF·steps/s of the explicit octree-SBFEM step on one GB300.
 
-Workload: the cube-with-spherical-cavity octree (levels 4-8, ~1.07M cells,
-~3.6M DOF, lognormal E_e, Ricker point load), one CDM step = the whole hot
-path (gather, K_p contraction, scatter, lumped-mass update, source term).
+One step = the whole hot path: gather, K_p contraction, scatter, source
+term, lumped-mass central-difference update.  Three forms are measured:
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32|mixed]
+* headline (``value``): the mixed-precision form (TF32x3 tensor-core
+  contraction, FP64 history) on the cube-with-spherical-cavity octree
+  (levels 4-8, ~1.02M cells, ~3.44M DOF, lognormal E_e, Ricker load);
+* ``forms.fp64``: the plain FP64 form on the same mesh;
+* ``forms.batched``: 64 load cases per launch (FP32 contraction, FP64
+  history) on the multi-point octree (levels 3-7, ~200k cells); its unit is
+  DOF·load-case·steps/s.
+
+Each form states its relative L2 error against the FP64 oracle after the
+same number of steps from the same start.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64|fp32]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
 Prints one JSON line (rank 0).  With torchrun (N > 1) every rank advances
-its own replica of the workload (the path is not sharded across GPUs here),
-value = all ranks' DOF·steps / the slowest rank's time.
+its own replica of the workload, value = all ranks' DOF·steps / the
+slowest rank's time.
 """
 from __future__ import annotations
 
@@ -34,10 +44,8 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def peaks():
@@ -48,21 +56,20 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
-def workload(rank=0):
-    import octree_gen as og
-    m = og.config_cavity_cube()
-    return m
+def algorithmic_bytes(mesh, nper, B=1):
+    """Per step: 32 B per DOF and load case (read U_n, U_{n-1}, write U_{n+1};
+    M^-1 once per DOF amortised) plus per cell 4 n_p (connectivity) + 8 (scale)
+    + 1 (op) B; the force kernel's own share: U_n (8 B per DOF and case) plus
+    the cell data."""
+    cell = int(np.sum(4 * nper + 9))
+    step = 24 * mesh.n_dof * B + 8 * mesh.n_dof + cell
+    force = 8 * mesh.n_dof * B + cell
+    return step, force
 
 
-def algorithmic_bytes_per_step(mesh, nper):
-    """32 B per DOF (read U_n, U_{n-1}, M^-1; write U_{n+1}) plus per cell
-    4 n_p B connectivity + 8 B scale + 1 B op."""
-    return 32 * mesh.n_dof + int(np.sum(4 * nper + 9))
-
-
-def contraction_flops(nper):
+def contraction_flops(nper, B=1):
     m = 3 * nper.astype(np.float64)
-    return float(np.sum(2 * m * m))
+    return float(np.sum(2 * m * m)) * B
 
 
 class ClockSampler:
@@ -109,31 +116,50 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(mesh, target_s=15.0, threads=None, u_start=None):
-    """The FP64 oracle (never tuned for this) on the host cores: a bounded
-    number of CDM steps of the same workload."""
+def time_steps(S, stream, steps, world, torch):
+    """CUDA events around step_n(steps) on the library's stream, barrier and
+    synchronize on both sides, max over ranks (ms)."""
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    S.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def oracle_reference(mesh, dt, n_steps, rhs=0, threads=None):
     from oracle import cdm
-    threads = threads or os.cpu_count() or 1
-    P = cdm.make_problem(mesh)
+    P = cdm.make_problem(mesh, dt=dt, rhs=rhs)
     u, up = cdm.initial_state(P)
     t = time.perf_counter()
-    u, up, _, _ = cdm.run(P, 2, u, up, threads=threads)
-    per = (time.perf_counter() - t) / 2
-    n = max(2, int(target_s / max(per, 1e-6)))
-    t = time.perf_counter()
-    u, up, _, _ = cdm.run(P, n, u, up, n0=2, threads=threads)
-    el = time.perf_counter() - t
-    return {"value": mesh.n_dof * n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "%d CDM steps (steps 2..%d) of the full workload, FP64 C oracle, OpenMP %d threads"
-                      % (n, n + 1, threads)}, P, n + 2, u
+    u, up, _, _ = cdm.run(P, n_steps, u, up, threads=threads or os.cpu_count() or 1)
+    return u, time.perf_counter() - t
+
+
+def gpu_after(S, n_steps, L):
+    S.initial()
+    S.step(n_steps)
+    return S.field(L.SBX_U_N)
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import octree_gen as og
     from oracle import cdm
-    mesh = workload()
+    mesh = og.config_cavity_cube()
     threads = os.cpu_count() or 1
     P = cdm.make_problem(mesh)
     u, up = cdm.initial_state(P)
@@ -146,7 +172,7 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": mesh.name, "cells": mesh.n_cells,
-                                           "dof": mesh.n_dof, "precision": "fp64"},
+                                           "dof": mesh.n_dof, "precision": "fp64 (oracle)"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                             "sample": "%d full CDM steps of the workload" % args.steps},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -157,19 +183,20 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default: 2000 for fp64, 20000 otherwise)")
+                    help="timed steps of the headline form (default 20000; reference: 20)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"],
+                    help="headline form on the cavity mesh")
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the extra forms (fp64 / batched) and the error runs")
     args = ap.parse_args()
-    if args.steps is None:
-        args.steps = 2000 if args.precision == "fp64" else 20000
-        if args.impl == "reference":
-            args.steps = 20
     if args.warmup < 3:
         args.warmup = 3
+    if args.steps is None:
+        args.steps = 20 if args.impl == "reference" else (2000 if args.precision == "fp64" else 20000)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -179,52 +206,31 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
+    import octree_gen as og
     from paper_2103_09100_gb300 import Solver, _lib as L, build
     build.build()
-    mesh = workload(rank)
-    stream = torch.cuda.Stream()
-    S = Solver.from_mesh(mesh, precision=args.precision, device=local, stream=stream.cuda_stream)
+    mesh = og.config_cavity_cube()
     nper = (mesh.slot_node >= 0).sum(1)
-    # per-cell node counts of the library's patterns (== mesh node counts)
+    stream = torch.cuda.Stream()
+    pk, pk_src = peaks()
+
+    # ---------------------------------------------------------- headline form
+    S = Solver.from_mesh(mesh, precision=args.precision, device=local, stream=stream.cuda_stream)
     S.initial()
     S.step(args.warmup)
     S.sync()
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
     clk = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    S.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    ms = time_steps(S, stream, args.steps, world, torch)
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
     S.sync()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     value = world * mesh.n_dof * args.steps / (ms * 1e-3)
 
-    # per-kernel device time, same kernels and shapes, events on the library stream
     prof_steps = min(args.steps, 200)
     ms_f, ms_u = L.sbx_profile(S.ctx, prof_steps, S.dt, S.alpha)
     t_force = ms_f / prof_steps * 1e-3
     t_update = ms_u / prof_steps * 1e-3
-    pk, pk_src = peaks()
     flops = contraction_flops(nper)
-    bytes_step = algorithmic_bytes_per_step(mesh, nper)
-    # the force kernel's own algorithmic bytes: U_n of every node (24 B) and
-    # the cell data (4 n_p + 9 B); the update kernel's: 32 B per DOF
-    bytes_force = 8 * mesh.n_dof + int(np.sum(4 * nper + 9))
-    bytes_update = 32 * mesh.n_dof
-    step_frac = (bytes_step / (t_force + t_update) / 1e9) / pk["hbm_gbs"]
+    bytes_step, bytes_force = algorithmic_bytes(mesh, nper)
     if args.precision == "fp64":
         ach = flops / t_force / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -236,18 +242,16 @@ def main():
         roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"], "traffic": None,
                 "kernel": "k_force_tc (all launch classes of one step)" if args.precision == "mixed"
-                else "k_force_simt<float>",
-                "peak_source": "hbm_gbs " + pk_src,
-                "tensor_tflops": 3 * flops / t_force / 1e12 if args.precision == "mixed" else None}
-    roof["algorithmic_bytes_per_launch"] = bytes_force
-    roof["force_ms"] = t_force * 1e3
-    roof["update_ms"] = t_update * 1e3
-    roof["update_hbm_frac"] = (bytes_update / t_update / 1e9) / pk["hbm_gbs"]
-    roof["step_bytes"] = bytes_step
-    roof["step_hbm_frac"] = step_frac
+                else "k_force_simt<float>", "peak_source": "hbm_gbs " + pk_src}
+        if args.precision == "mixed":
+            roof["tensor_tflops_tf32"] = 3 * flops / t_force / 1e12
+    roof.update({"algorithmic_bytes_per_launch": bytes_force, "force_ms": t_force * 1e3,
+                 "update_ms": t_update * 1e3,
+                 "update_hbm_frac": (32 * mesh.n_dof / t_update / 1e9) / pk["hbm_gbs"],
+                 "step_bytes": bytes_step,
+                 "step_hbm_frac": (bytes_step / (t_force + t_update) / 1e9) / pk["hbm_gbs"]})
 
-    # end to end through the C ABI with host buffers: upload the state from
-    # pinned host memory, run e2e_steps steps, read the field back
+    # end to end through the C ABI with host buffers
     nd = mesh.n_dof
     h_un = torch.empty(nd, dtype=torch.float64).pin_memory()
     h_um = torch.empty(nd, dtype=torch.float64).pin_memory()
@@ -266,6 +270,7 @@ def main():
            "d2h_bytes_per_step": nd * 8 / args.e2e_steps,
            "how": "write_field(U_n), write_field(U_n-1) from pinned host, step_n(%d), "
                   "read_field(U_n) to pinned host" % args.e2e_steps}
+    gpu_launches = L.sbx_query(S.ctx, L.SBX_Q_KERNELS_PER_STEP) * args.steps
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -278,21 +283,82 @@ def main():
                       "precision": args.precision, "dt": S.dt,
                       "l2": "per-step working set %.0f MB > L2; no flush" % (bytes_step / 1e6),
                       "parallelism": "replicas" if world > 1 else "1 GPU"},
-           "roofline": roof, "gpu_launches": L.sbx_query(S.ctx, L.SBX_Q_KERNELS_PER_STEP) * args.steps,
-           "clocks": clocks, "e2e": e2e}
+           "roofline": roof, "gpu_launches": gpu_launches, "clocks": clocks, "e2e": e2e}
+
+    forms = {}
+    if rank == 0 and not args.headline_only:
+        # relative error of the headline form after n_err steps from rest
+        n_err = 150
+        u_ref, _ = oracle_reference(mesh, S.dt, n_err)
+        g = gpu_after(S, n_err, L)
+        forms[args.precision] = {"value": value, "unit": UNIT, "ms_per_step": ms / args.steps,
+                                 "rel_err_vs_oracle": float(np.linalg.norm(g - u_ref) / np.linalg.norm(u_ref)),
+                                 "err_steps": n_err}
+        S.close()
+        # plain FP64 form on the same mesh
+        if args.precision != "fp64":
+            F = Solver.from_mesh(mesh, precision="fp64", device=local, stream=stream.cuda_stream, dt=S.dt)
+            F.initial()
+            F.step(3)
+            k = 1000
+            msf = time_steps(F, stream, k, world, torch)
+            gf = gpu_after(F, n_err, L)
+            forms["fp64"] = {"value": world * mesh.n_dof * k / (msf * 1e-3), "unit": UNIT,
+                             "ms_per_step": msf / k, "steps": k,
+                             "rel_err_vs_oracle": float(np.linalg.norm(gf - u_ref) / np.linalg.norm(u_ref)),
+                             "err_steps": n_err}
+            F.close()
+        # batched form: 64 load cases on the multi-point octree
+        mb = og.config_multi_point()
+        B = 64
+        Bs = Solver.from_mesh(mb, precision="fp32", n_rhs=B, device=local, stream=stream.cuda_stream)
+        Bs.initial()
+        Bs.step(3)
+        kb = 200
+        msb = time_steps(Bs, stream, kb, world, torch)
+        nb_err = 100
+        gb = gpu_after(Bs, nb_err, L).reshape(-1, B)
+        errs = []
+        for b in (0, 37):
+            ub, _ = oracle_reference(mb, Bs.dt, nb_err, rhs=b)
+            errs.append(float(np.linalg.norm(gb[:, b] - ub) / np.linalg.norm(ub)))
+        nperb = (mb.slot_node >= 0).sum(1)
+        ms_fb, ms_ub = L.sbx_profile(Bs.ctx, 20, Bs.dt, Bs.alpha)
+        bb_step, bb_force = algorithmic_bytes(mb, nperb, B)
+        forms["batched"] = {"value": world * mb.n_dof * B * kb / (msb * 1e-3),
+                            "unit": "DOF*load_cases*steps/s", "load_cases": B,
+                            "ms_per_step": msb / kb, "steps": kb,
+                            "workload": mb.name + " (%d cells, %d DOF)" % (mb.n_cells, mb.n_dof),
+                            "precision": "f32 contraction, f64 state",
+                            "force_ms": ms_fb / 20, "update_ms": ms_ub / 20,
+                            "step_hbm_frac": (bb_step / ((ms_fb + ms_ub) / 20 * 1e-3) / 1e9) / pk["hbm_gbs"],
+                            "fp32_gflops": contraction_flops(nperb, B) / (ms_fb / 20 * 1e-3) / 1e9,
+                            "rel_err_vs_oracle_max": max(errs), "err_cases": [0, 37],
+                            "err_steps": nb_err}
+        Bs.close()
+        out["forms"] = forms
+        out["rel_err_vs_oracle"] = forms[args.precision]["rel_err_vs_oracle"]
+    else:
+        S.close()
 
     if rank == 0 and not args.no_cpu_baseline:
-        cb, P, n_ref, u_ref = cpu_baseline(mesh)
-        # same steps on the GPU from the same start: stated relative error
-        S.initial()
-        S.step(n_ref)
-        g = S.field(L.SBX_U_N)
-        out["cpu_baseline"] = cb
-        out["rel_err_vs_oracle"] = {"steps": n_ref,
-                                    "rel_l2": float(np.linalg.norm(g - u_ref) / np.linalg.norm(u_ref))}
+        from oracle import cdm
+        threads = os.cpu_count() or 1
+        P = cdm.make_problem(mesh)
+        u, up = cdm.initial_state(P)
+        t = time.perf_counter()
+        u, up, _, _ = cdm.run(P, 2, u, up, threads=threads)
+        per = (time.perf_counter() - t) / 2
+        n = max(2, int(15.0 / max(per, 1e-6)))
+        t = time.perf_counter()
+        cdm.run(P, n, u, up, n0=2, threads=threads)
+        el = time.perf_counter() - t
+        out["cpu_baseline"] = {"value": mesh.n_dof * n / el, "unit": UNIT, "cores": threads,
+                               "kind": "oracle",
+                               "sample": "%d CDM steps (steps 2..%d) of the full cavity workload, "
+                                         "FP64 C oracle, OpenMP %d threads" % (n, n + 1, threads)}
     if rank == 0:
         print(json.dumps(out), flush=True)
-    S.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -201,6 +201,41 @@ int sbx_profile(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha,
                 double *ms_force, double *ms_update);
 
 /*
+ * set_modulus: replace every cell's Young's modulus E_e (K_e = E_e h_e T^T K_p T,
+ * Eq. KM_scale) without re-uploading the mesh.  E[C] in the caller's cell
+ * order of mesh_upload, all > 0.  The lumped mass does not depend on E.
+ * Supported for single-load-case meshes in SBX_PREC_FP64 / SBX_PREC_FP32.
+ *   Errors: SBX_ESTATE (no mesh), SBX_EINVAL (values, mode).
+ */
+int set_modulus(sbx_ctx *ctx, const double *E);
+
+/*
+ * sbx_adjoint: misfit of receiver time histories and its gradient with
+ * respect to every cell's modulus, by the exact discrete adjoint of the
+ * undamped recurrence (alpha = 0):
+ *   J = 1/2 sum_{n=1..N} sum_r (U_n[rec_r] - data[(n-1) n_rec + r])^2,
+ *   lambda_n = g_n + (2 I - K W) lambda_{n+1} - lambda_{n+2},  W = dt^2 M^-1,
+ *   dJ/dE_e = -h_e sum_{n=0}^{N-1} (W lambda_{n+1})_e^T T^T K_p T U_{n,e}.
+ * Starts from the state set by set_initial (step index 0), which must be at
+ * rest (U_0 = 0, Udot_0 = 0) so that U_-1 does not depend on the moduli.
+ * The forward run stores (U_n, U_{n-1}) every ckpt_every steps; the reverse
+ * sweep recomputes each segment from its checkpoint.  Device memory for
+ * (N / ckpt_every + 1) checkpoints and ckpt_every + 1 states is allocated
+ * for the call and freed before it returns.
+ *   n_steps N >= 1, dt > 0, n_rec >= 0, rec_dof[n_rec] DOF indices,
+ *   data[N * n_rec], ckpt_every >= 1.  Outputs: *misfit_out = J,
+ *   grad_E_out[C] in the caller's cell order.  Afterwards the state is
+ *   reset to the starting state (step 0).  Single-load-case meshes in
+ *   SBX_PREC_FP64 or SBX_PREC_FP32 (the contraction runs in that precision,
+ *   the recurrences and the gradient sums in FP64).
+ *   Errors: SBX_ESTATE (no mesh, step index not 0), SBX_EINVAL, SBX_ENOMEM,
+ *   SBX_ECUDA, SBX_ENONFINITE.
+ */
+int sbx_adjoint(sbx_ctx *ctx, int64_t n_steps, double dt, int64_t n_rec,
+                const int64_t *rec_dof, const double *data, int64_t ckpt_every,
+                double *misfit_out, double *grad_E_out);
+
+/*
  * sbx_query: diagnostics about the uploaded mesh and the launch plan.
  *   what = SBX_Q_KERNELS_PER_STEP  kernel launches per step (force + update)
  *          SBX_Q_FORCE_LAUNCHES    force-kernel launches per step

@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "SBX_OK", 1: "SBX_EINVAL", 2: "SBX_ENOMEM", 3: "SBX_ECUDA",
 # every symbol include/sbx.h declares
 EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patterns",
            "mesh_upload", "set_load", "set_initial", "step_n", "sbx_get_step", "sbx_set_step",
-           "read_field", "write_field", "sbx_profile", "sbx_query", "sbx_step_static"]
+           "read_field", "write_field", "sbx_profile", "sbx_query", "sbx_step_static",
+           "set_modulus", "sbx_adjoint"]
 SBX_Q_KERNELS_PER_STEP, SBX_Q_FORCE_LAUNCHES, SBX_Q_TILES = 0, 1, 2
 SBX_STATIC_MAX_DOF = 4 * 1024 * 1024
 SBX_STATIC_MAX_PATTERNS = 144
@@ -65,6 +66,8 @@ def load(path: str = LIB_PATH):
         "sbx_profile": [vp, i64, dbl, dbl, C.POINTER(dbl), C.POINTER(dbl)],
         "sbx_step_static": [vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, dbl, vp, vp],
         "sbx_query": [vp, i32, C.POINTER(i64)],
+        "set_modulus": [vp, vp],
+        "sbx_adjoint": [vp, i64, dbl, i64, vp, vp, i64, C.POINTER(dbl), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -145,6 +148,19 @@ def set_initial(ctx, u0, v0, dt, alpha=0.0):
 
 def step_n(ctx, n_steps, dt, alpha=0.0):
     _check(ctx, load().step_n(ctx, int(n_steps), float(dt), float(alpha)))
+
+
+def set_modulus(ctx, E):
+    _check(ctx, load().set_modulus(ctx, _ptr(E, np.float64)))
+
+
+def sbx_adjoint(ctx, n_steps, dt, rec_dof, data, ckpt_every, grad_out):
+    """Returns the misfit J; grad_out (one double per cell) receives dJ/dE."""
+    J = C.c_double()
+    _check(ctx, load().sbx_adjoint(ctx, int(n_steps), float(dt), len(rec_dof),
+                                   _ptr(rec_dof, np.int64), _ptr(data, np.float64),
+                                   int(ckpt_every), C.byref(J), _ptr(grad_out, np.float64)))
+    return J.value
 
 
 def sbx_query(ctx, what) -> int:

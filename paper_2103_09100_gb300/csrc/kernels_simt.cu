@@ -145,18 +145,20 @@ static size_t simt_smem(int m, bool fp32) {
 }
 
 cudaError_t launch_force_simt(const sbx_ctx *ctx, const double *u, double *f, double dt,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool with_loads) {
   const bool fp32 = ctx->prec == SBX_PREC_FP32;
   const size_t smem = simt_smem(ctx->max_m, fp32);
   if (ctx->n_tiles_simt == 0) return cudaSuccess;
+  LoadTable L = ctx->loads();
+  if (!with_loads) L.n = 0;
   if (fp32) {
     auto k = k_force_simt<float, SIMT_TILE>;
-    k<<<ctx->n_tiles_simt, 256, smem, s>>>(ctx->d_tiles_simt, ctx->view(), ctx->d_K32, u, f,
-                                           ctx->loads(), ctx->d_step, dt);
+    k<<<ctx->n_tiles_simt, 256, smem, s>>>(ctx->d_tiles_simt, ctx->view(), ctx->d_K32, u, f, L,
+                                           ctx->d_step, dt);
   } else {
     auto k = k_force_simt<double, SIMT_TILE>;
-    k<<<ctx->n_tiles_simt, 256, smem, s>>>(ctx->d_tiles_simt, ctx->view(), ctx->d_K64, u, f,
-                                           ctx->loads(), ctx->d_step, dt);
+    k<<<ctx->n_tiles_simt, 256, smem, s>>>(ctx->d_tiles_simt, ctx->view(), ctx->d_K64, u, f, L,
+                                           ctx->d_step, dt);
   }
   return cudaGetLastError();
 }

@@ -226,7 +226,7 @@ int sbx_create(sbx_ctx **out, int device, void *cuda_stream) {
     ctx->own_stream = true;
   }
   if (sbx::prepare_kernels() != cudaSuccess || sbx::prepare_tc_kernels() != cudaSuccess ||
-      sbx::prepare_batch_kernels() != cudaSuccess) {
+      sbx::prepare_batch_kernels() != cudaSuccess || sbx::prepare_adjoint_kernels() != cudaSuccess) {
     cudaGetLastError();
     sbx_destroy(ctx);
     return SBX_ECUDA;
@@ -464,6 +464,9 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   ctx->B = n_rhs;
   ctx->prec = precision_mode;
   ctx->pat_cstart = start;
+  ctx->h_order = order;
+  ctx->h_hs.resize(n_cells);
+  for (int64_t s = 0; s < n_cells; ++s) ctx->h_hs[s] = hv[order[s]];
   ctx->pat_ccount = cnt;
   ctx->n_tiles_simt = (int)tiles.size();
   ctx->max_m = max_m;
@@ -646,6 +649,148 @@ int sbx_profile(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha, double *
   *ms_update = tu;
   if (rc) return rc;
   return check_flags(ctx);
+}
+
+int set_modulus(sbx_ctx *ctx, const double *E) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
+  if (ctx->B != 1 || ctx->prec == SBX_PREC_MIXED)
+    return fail(ctx, SBX_EINVAL, "set_modulus needs a single-load-case FP64 or FP32 mesh");
+  std::vector<double> Ev;
+  if (int rc = fetch_vec(ctx, Ev, E, ctx->C)) return rc;
+  std::vector<double> scale(ctx->C);
+  for (int64_t s = 0; s < ctx->C; ++s) {
+    const double e = Ev[ctx->h_order[s]];
+    if (!(e > 0) || !isfinite(e)) return fail(ctx, SBX_EINVAL, "E must be positive and finite");
+    scale[s] = e * ctx->h_hs[s];
+  }
+  CK(cudaMemcpyAsync(ctx->d_scale, scale.data(), scale.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SBX_OK;
+}
+
+int sbx_adjoint(sbx_ctx *ctx, int64_t n_steps, double dt, int64_t n_rec, const int64_t *rec_dof,
+                const double *data, int64_t ckpt_every, double *misfit_out, double *grad_E_out) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
+  if (ctx->step != 0) return fail(ctx, SBX_ESTATE, "sbx_adjoint starts from set_initial (step 0)");
+  if (ctx->B != 1 || ctx->prec == SBX_PREC_MIXED)
+    return fail(ctx, SBX_EINVAL, "sbx_adjoint needs a single-load-case FP64 or FP32 mesh");
+  if (n_steps < 1 || !(dt > 0) || n_rec < 0 || ckpt_every < 1 || !misfit_out || !grad_E_out ||
+      (n_rec > 0 && (!rec_dof || !data)))
+    return fail(ctx, SBX_EINVAL, "bad adjoint arguments");
+  const int64_t nd = ctx->ndof, N = n_steps, k = std::min(ckpt_every, n_steps);
+  std::vector<int64_t> rec;
+  std::vector<double> dat;
+  if (int rc = fetch_vec(ctx, rec, rec_dof, n_rec)) return rc;
+  for (int64_t r : rec)
+    if (r < 0 || r >= nd) return fail(ctx, SBX_EINVAL, "receiver DOF out of range");
+  if (int rc = fetch_vec(ctx, dat, data, (size_t)(N * n_rec))) return rc;
+  const int64_t nseg = (N + k - 1) / k;
+  int64_t *d_rec = nullptr;
+  double *d_dat = nullptr, *d_ck = nullptr, *d_seg = nullptr, *d_lam = nullptr, *d_v = nullptr,
+         *d_acc = nullptr, *d_J = nullptr;
+  auto release = [&]() {
+    dfree(d_rec); dfree(d_dat); dfree(d_ck); dfree(d_seg); dfree(d_lam); dfree(d_v);
+    dfree(d_acc); dfree(d_J);
+  };
+  int rc = SBX_OK;
+  if (!rc) rc = upload(ctx, &d_rec, rec);
+  if (!rc) rc = upload(ctx, &d_dat, dat);
+  if (!rc) rc = dalloc(ctx, &d_ck, (size_t)(nseg * 2 * nd));
+  if (!rc) rc = dalloc(ctx, &d_seg, (size_t)((k + 1) * nd));
+  if (!rc) rc = dalloc(ctx, &d_lam, (size_t)(3 * nd));
+  if (!rc) rc = dalloc(ctx, &d_v, (size_t)nd);
+  if (!rc) rc = dalloc(ctx, &d_acc, (size_t)ctx->C);
+  if (!rc) rc = dalloc(ctx, &d_J, 1);
+  if (rc) {
+    release();
+    return rc;
+  }
+  const size_t vb = nd * sizeof(double);
+  cudaStream_t s = ctx->stream;
+  auto go = [&]() -> int {
+    CK(sbx::prepare_update(ctx, dt, 0.0, s));
+    if (ctx->f_dirty) {
+      CK(cudaMemsetAsync(ctx->d_f, 0, vb, s));
+      ctx->f_dirty = false;
+    }
+    // forward with checkpoints (U_{sk}, U_{sk-1})
+    for (int64_t g = 0; g < nseg; ++g) {
+      CK(cudaMemcpyAsync(d_ck + (2 * g) * nd, ctx->d_u[ctx->cur], vb, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(d_ck + (2 * g + 1) * nd, ctx->d_u[ctx->cur ^ 1], vb,
+                         cudaMemcpyDeviceToDevice, s));
+      const int64_t len = std::min(k, N - g * k);
+      for (int64_t j = 0; j < len; ++j) {
+        if (int r = one_step(ctx, ctx->cur, dt, 0.0, 1)) return r;
+        ctx->cur ^= 1;
+      }
+    }
+    CK(cudaMemsetAsync(d_lam, 0, 3 * vb, s));
+    CK(cudaMemsetAsync(d_acc, 0, ctx->C * sizeof(double), s));
+    CK(cudaMemsetAsync(d_J, 0, sizeof(double), s));
+    double *lam1 = d_lam, *lam2 = d_lam + nd, *spare = d_lam + 2 * nd;   // lambda_{n+1}, _{n+2}
+    (void)spare;
+    for (int64_t g = nseg - 1; g >= 0; --g) {
+      // recompute U_{gk} .. U_{gk+len} into the segment buffer
+      CK(cudaMemcpyAsync(ctx->d_u[0], d_ck + (2 * g) * nd, vb, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(ctx->d_u[1], d_ck + (2 * g + 1) * nd, vb, cudaMemcpyDeviceToDevice, s));
+      ctx->cur = 0;
+      const int64_t n0 = g * k;
+      CK(cudaMemcpyAsync(ctx->d_step, &n0, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(d_seg, ctx->d_u[0], vb, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemsetAsync(ctx->d_f, 0, vb, s));   // holds K W lambda from the reverse sweep
+      const int64_t len = std::min(k, N - n0);
+      for (int64_t j = 1; j <= len; ++j) {
+        if (int r = one_step(ctx, ctx->cur, dt, 0.0, 1)) return r;
+        ctx->cur ^= 1;
+        CK(cudaMemcpyAsync(d_seg + j * nd, ctx->d_u[ctx->cur], vb, cudaMemcpyDeviceToDevice, s));
+      }
+      for (int64_t n = n0 + len; n >= n0 + 1; --n) {
+        // lambda_n = g_n + 2 lambda_{n+1} - K (W lambda_{n+1}) - lambda_{n+2}  (into lam2)
+        CK(sbx::launch_weight(ctx, lam1, d_v, s));
+        CK(cudaMemsetAsync(ctx->d_f, 0, vb, s));
+        CK(sbx::launch_force_simt(ctx, d_v, ctx->d_f, dt, s, false));
+        CK(sbx::launch_adj_update(ctx, ctx->d_f, lam1, lam2, s));
+        CK(sbx::launch_residual(ctx, n_rec, d_rec, d_seg + (n - n0) * nd, d_dat + (n - 1) * n_rec,
+                                lam2, d_J, s));
+        // dJ/dE pair (lambda_n, U_{n-1})
+        CK(sbx::launch_weight(ctx, lam2, d_v, s));
+        CK(sbx::launch_grad(ctx, d_seg + (n - 1 - n0) * nd, d_v, d_acc, s));
+        std::swap(lam1, lam2);   // lambda_{n+1} <- lambda_n, lambda_{n+2} <- old lambda_{n+1}
+      }
+    }
+    // back to the starting state
+    CK(cudaMemcpyAsync(ctx->d_u[0], d_ck, vb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_u[1], d_ck + nd, vb, cudaMemcpyDeviceToDevice, s));
+    ctx->cur = 0;
+    const int64_t zero = 0;
+    CK(cudaMemcpyAsync(ctx->d_step, &zero, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_f, 0, vb, s));
+    std::vector<double> acc(ctx->C);
+    double J = 0.0;
+    CK(cudaMemcpyAsync(acc.data(), d_acc, ctx->C * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&J, d_J, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<double> grad(ctx->C);
+    for (int64_t q = 0; q < ctx->C; ++q) grad[ctx->h_order[q]] = -ctx->h_hs[q] * acc[q];
+    if (is_device_ptr(grad_E_out)) {
+      CK(cudaMemcpy(grad_E_out, grad.data(), ctx->C * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+      memcpy(grad_E_out, grad.data(), ctx->C * sizeof(double));
+    }
+    *misfit_out = J;
+    return check_flags(ctx);
+  };
+  rc = go();
+  ctx->step = 0;
+  release();
+  return rc;
 }
 
 int sbx_query(sbx_ctx *ctx, int what, int64_t *out) {

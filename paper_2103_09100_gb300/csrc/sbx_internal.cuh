@@ -91,6 +91,8 @@ struct sbx_ctx {
   int64_t N = 0, C = 0, ndof = 0;  // ndof = 3 N (one load case)
   int B = 1, prec = SBX_PREC_FP64;
   std::vector<int64_t> pat_cstart, pat_ccount;
+  std::vector<int64_t> h_order;      // sorted position -> caller's cell index
+  std::vector<double> h_hs;          // edge length per sorted cell
   int32_t *d_conn = nullptr;
   int64_t *d_conn_off = nullptr, *d_pat_cstart = nullptr, *d_pat_ccount = nullptr;
   uint8_t *d_sym = nullptr;
@@ -150,7 +152,17 @@ namespace sbx {
 // kernels_simt.cu
 constexpr int SIMT_TILE = 32;
 cudaError_t launch_force_simt(const sbx_ctx *ctx, const double *u, double *f, double dt,
-                              cudaStream_t s);
+                              cudaStream_t s, bool with_loads = true);
+// kernels_adjoint.cu
+cudaError_t launch_weight(const sbx_ctx *ctx, const double *lam, double *v, cudaStream_t s);
+cudaError_t launch_adj_update(const sbx_ctx *ctx, const double *f, const double *lam1,
+                              double *lam2_to_lam, cudaStream_t s);
+cudaError_t launch_residual(const sbx_ctx *ctx, int64_t n_rec, const int64_t *rec,
+                            const double *u_n, const double *data_n, double *lam, double *J,
+                            cudaStream_t s);
+cudaError_t launch_grad(const sbx_ctx *ctx, const double *u, const double *v, double *acc,
+                        cudaStream_t s);
+cudaError_t prepare_adjoint_kernels();
 // w = dt^2 M^-1 / (1 + alpha dt / 2) for the update; recomputed when dt or
 // alpha change (outside stream capture).
 cudaError_t prepare_update(sbx_ctx *ctx, double dt, double alpha, cudaStream_t s);

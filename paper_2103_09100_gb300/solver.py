@@ -24,6 +24,7 @@ class Solver:
                  precision="fp64", n_rhs=1, device=0, stream=None, dt=None, dt_factor=0.5,
                  alpha=0.0):
         self.n_nodes = int(n_nodes)
+        self.n_cells = int(len(mask))
         self.n_rhs = int(n_rhs)
         self.precision = precision
         masters, cell_pattern, cell_sym, cell_ptr, cell_nodes = patterns.classify_mesh(
@@ -88,6 +89,20 @@ class Solver:
 
     def sync(self):
         L.sbx_sync(self.ctx)
+
+    def set_modulus(self, E):
+        """New Young's modulus per cell (caller's cell order)."""
+        L.set_modulus(self.ctx, np.ascontiguousarray(E, np.float64))
+
+    def adjoint(self, n_steps, rec_dof, data, ckpt_every=64):
+        """(J, dJ/dE) of J = 1/2 sum_n sum_r (U_n[rec] - data[n-1, r])^2 over
+        n_steps steps from the state of ``initial()`` (which must be at rest),
+        by the GPU discrete adjoint with a checkpoint every ``ckpt_every``
+        steps."""
+        grad = np.empty(self.n_cells)
+        J = L.sbx_adjoint(self.ctx, n_steps, self.dt, np.ascontiguousarray(rec_dof, np.int64),
+                          np.ascontiguousarray(data, np.float64).ravel(), ckpt_every, grad)
+        return J, grad
 
     def close(self):
         if self.ctx is not None:
