@@ -13,6 +13,7 @@
 // a broadcast and 32 distinct displacement entries.
 #include <math.h>
 
+#include "device_common.cuh"
 #include "sbx_internal.cuh"
 
 namespace sbx {
@@ -231,6 +232,62 @@ static int update_grid(int64_t nd) {
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
+// Mixed form: f is float [N][4]; one thread per node.  FP32 -> FP64 by bit
+// re-packing, and U_{n+1} split into FP32 (hi, lo) for the next force
+// evaluation, with integer operations (both off the FP64 pipe).
+__device__ __forceinline__ void put_pair(float *p, double x0, double x1, double x2) {
+  float h0, h1, h2, l0, l1, l2;
+  split_f64(x0, h0, l0);
+  split_f64(x1, h1, l1);
+  split_f64(x2, h2, l2);
+  float2 *q = reinterpret_cast<float2 *>(p);   // 6 floats, 8-byte aligned
+  q[0] = make_float2(h0, h1);
+  q[1] = make_float2(h2, l0);
+  q[2] = make_float2(l1, l2);
+}
+
+template <bool DAMPED>
+__global__ void __launch_bounds__(256) k_update_f32(int64_t nn, const double *__restrict__ w,
+                                                    float4 *__restrict__ f,
+                                                    const double *__restrict__ uc,
+                                                    double *__restrict__ up,
+                                                    float *__restrict__ pairs, double a, double b,
+                                                    int zero_f, int32_t *flags, int64_t *d_step) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 fv = f[i];
+    const int64_t o = 3 * i;
+    const double r0 = cdm_update<DAMPED>(w[o], f2d_bits(fv.x), uc[o], up[o], a, b);
+    const double r1 = cdm_update<DAMPED>(w[o + 1], f2d_bits(fv.y), uc[o + 1], up[o + 1], a, b);
+    const double r2 = cdm_update<DAMPED>(w[o + 2], f2d_bits(fv.z), uc[o + 2], up[o + 2], a, b);
+    bad |= nonfinite(r0) || nonfinite(r1) || nonfinite(r2);
+    up[o] = r0;
+    up[o + 1] = r1;
+    up[o + 2] = r2;
+    put_pair(pairs + 6 * i, r0, r1, r2);
+    if (zero_f) f[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *d_step += 1;
+}
+
+__global__ void k_split_pairs(int64_t nn, const double *u, float *pairs) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
+       i += (int64_t)gridDim.x * blockDim.x)
+    put_pair(pairs + 6 * i, u[3 * i], u[3 * i + 1], u[3 * i + 2]);
+}
+
+__global__ void k_widen_f32(int64_t nn, const float4 *f, double *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = f[i];
+    out[3 * i] = f2d_bits(v.x);
+    out[3 * i + 1] = f2d_bits(v.y);
+    out[3 * i + 2] = f2d_bits(v.z);
+  }
+}
+
 __global__ void k_make_w(int64_t nd, const double *minv, double *w, double c) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -261,6 +318,33 @@ cudaError_t launch_update(const sbx_ctx *ctx, const double *uc, double *up, doub
   else
     k_update<true><<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_w, f, uc, up, 2.0 / cp, cm / cp,
                                                    zero_f, ctx->d_flags, ctx->d_step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_f32(const sbx_ctx *ctx, const double *uc, double *up, float *f4,
+                              float *pairs_out, double dt, double alpha, int zero_f,
+                              cudaStream_t s) {
+  const int64_t nn = ctx->N;
+  const double cm = 1.0 - 0.5 * alpha * dt, cp = 1.0 + 0.5 * alpha * dt;
+  float4 *f = reinterpret_cast<float4 *>(f4);
+  if (alpha == 0.0)
+    k_update_f32<false><<<update_grid(2 * nn), 256, 0, s>>>(
+        nn, ctx->d_w, f, uc, up, pairs_out, 2.0, 1.0, zero_f, ctx->d_flags, ctx->d_step);
+  else
+    k_update_f32<true><<<update_grid(2 * nn), 256, 0, s>>>(
+        nn, ctx->d_w, f, uc, up, pairs_out, 2.0 / cp, cm / cp, zero_f, ctx->d_flags,
+        ctx->d_step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_pairs(const sbx_ctx *ctx, const double *u, float *pairs, cudaStream_t s) {
+  k_split_pairs<<<update_grid(2 * ctx->N), 256, 0, s>>>(ctx->N, u, pairs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen_f32(const sbx_ctx *ctx, const float *f4, double *out, cudaStream_t s) {
+  k_widen_f32<<<update_grid(2 * ctx->N), 256, 0, s>>>(
+      ctx->N, reinterpret_cast<const float4 *>(f4), out);
   return cudaGetLastError();
 }
 

@@ -110,7 +110,10 @@ void free_mesh(sbx_ctx *ctx) {
   dfree(ctx->d_sym); dfree(ctx->d_scale); dfree(ctx->d_minv); dfree(ctx->d_mass);
   dfree(ctx->d_w);
   ctx->w_valid = false;
-  dfree(ctx->d_u[0]); dfree(ctx->d_u[1]); dfree(ctx->d_f); dfree(ctx->d_tiles_simt);
+  dfree(ctx->d_u[0]); dfree(ctx->d_u[1]); dfree(ctx->d_f); dfree(ctx->d_fx);
+  dfree(ctx->d_pair[0]); dfree(ctx->d_pair[1]);
+  ctx->pair_valid[0] = ctx->pair_valid[1] = false;
+  dfree(ctx->d_tiles_simt);
   dfree(ctx->d_load_dof); dfree(ctx->d_load_amp); dfree(ctx->d_load_t1); dfree(ctx->d_load_ncyc);
   dfree(ctx->d_load_kind);
   dfree(ctx->d_tc_pat); dfree(ctx->d_tc_K); dfree(ctx->d_tc_rec);
@@ -141,7 +144,13 @@ int force(sbx_ctx *ctx, const double *u, double *f, double dt) {
   if (ctx->B > 1) {
     CK(sbx::launch_force_batch(ctx, u, f, dt, ctx->stream));
   } else if (ctx->prec == SBX_PREC_MIXED) {
-    CK(sbx::launch_force_tc(ctx, u, f, dt, ctx->stream));
+    const int p = u == ctx->d_u[0] ? 0 : (u == ctx->d_u[1] ? 1 : -1);
+    if (p < 0) return fail(ctx, SBX_EINVAL, "the mixed force runs on the state buffers only");
+    if (!ctx->pair_valid[p]) {
+      CK(sbx::launch_split_pairs(ctx, u, ctx->d_pair[p], ctx->stream));
+      ctx->pair_valid[p] = true;
+    }
+    CK(sbx::launch_force_tc(ctx, ctx->d_pair[p], reinterpret_cast<float *>(f), dt, ctx->stream));
   } else {
     CK(sbx::launch_force_simt(ctx, u, f, dt, ctx->stream));
   }
@@ -151,9 +160,23 @@ int force(sbx_ctx *ctx, const double *u, double *f, double dt) {
 int update(sbx_ctx *ctx, const double *uc, double *up, double dt, double alpha, int zero_f) {
   if (ctx->B > 1) {
     CK(sbx::launch_update_batch(ctx, uc, up, ctx->d_f, dt, alpha, zero_f, ctx->stream));
+  } else if (ctx->prec == SBX_PREC_MIXED) {
+    const int p = up == ctx->d_u[0] ? 0 : 1;
+    CK(sbx::launch_update_f32(ctx, uc, up, reinterpret_cast<float *>(ctx->d_f), ctx->d_pair[p], dt,
+                              alpha, zero_f, ctx->stream));
+    ctx->pair_valid[p] = true;
   } else {
     CK(sbx::launch_update(ctx, uc, up, ctx->d_f, dt, alpha, zero_f, ctx->stream));
   }
+  return SBX_OK;
+}
+
+// Mixed form: make the (hi, lo) pairs of U_n current before replaying a
+// graph (the captured steps take them from the previous update).
+int ensure_pairs(sbx_ctx *ctx) {
+  if (ctx->prec != SBX_PREC_MIXED || ctx->B != 1 || ctx->pair_valid[ctx->cur]) return SBX_OK;
+  CK(sbx::launch_split_pairs(ctx, ctx->d_u[ctx->cur], ctx->d_pair[ctx->cur], ctx->stream));
+  ctx->pair_valid[ctx->cur] = true;
   return SBX_OK;
 }
 
@@ -431,12 +454,16 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   if (!rc) rc = dalloc(ctx, &ctx->d_u[1], nfield);
   if (!rc) rc = dalloc(ctx, &ctx->d_f, nfield);
   if (!rc) rc = dalloc(ctx, &ctx->d_w, ndof);
+  if (!rc && precision_mode == SBX_PREC_MIXED && n_rhs == 1) rc = dalloc(ctx, &ctx->d_fx, ndof);
+  if (!rc && precision_mode == SBX_PREC_MIXED && n_rhs == 1) rc = dalloc(ctx, &ctx->d_pair[0], 2 * ndof);
+  if (!rc && precision_mode == SBX_PREC_MIXED && n_rhs == 1) rc = dalloc(ctx, &ctx->d_pair[1], 2 * ndof);
   if (rc) {
     free_mesh(ctx);
     return rc;
   }
   ctx->prec = precision_mode;
   ctx->B = n_rhs;
+  ctx->N = n_nodes;
   if (n_rhs > 1) {
     std::string e;
     const int brc = sbx::batch_setup(ctx, conn, conn_off, cnt, ssym, scale, start, e);
@@ -542,6 +569,7 @@ int set_initial(sbx_ctx *ctx, const double *u0, const double *v0, double dt, dou
   const int64_t nd = ctx->ndof * ctx->B;
   const size_t bytes = nd * sizeof(double);
   ctx->cur = 0;
+  ctx->pair_valid[0] = ctx->pair_valid[1] = false;
   double *U0 = ctx->d_u[0], *Um1 = ctx->d_u[1];
   if (u0) {
     CK(cudaMemcpyAsync(U0, u0, bytes, cudaMemcpyDefault, ctx->stream));
@@ -559,8 +587,14 @@ int set_initial(sbx_ctx *ctx, const double *u0, const double *v0, double dt, dou
   CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(int64_t), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_f, 0, bytes, ctx->stream));
   if (int rc = force(ctx, U0, ctx->d_f, dt)) return rc;
+  const double *F0 = ctx->d_f;
+  if (ctx->prec == SBX_PREC_MIXED && ctx->B == 1) {
+    CK(sbx::launch_widen_f32(ctx, reinterpret_cast<const float *>(ctx->d_f), ctx->d_fx,
+                             ctx->stream));
+    F0 = ctx->d_fx;
+  }
   // k_init_um1 reads v0[i] before writing um1[i] of the same index
-  CK(sbx::launch_init_um1(ctx, U0, V0, Um1, ctx->d_f, dt, alpha, ctx->stream));
+  CK(sbx::launch_init_um1(ctx, U0, V0, Um1, F0, dt, alpha, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_f, 0, bytes, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t), ctx->stream));
   ctx->step = 0;
@@ -582,6 +616,7 @@ int step_n(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha) {
     ctx->f_dirty = false;
   }
   CK(sbx::prepare_update(ctx, dt, alpha, ctx->stream));
+  if (int rc = ensure_pairs(ctx)) return rc;
   int64_t left = n_steps - 1;  // the last step keeps R_int for read-back
   if (left >= GRAPH_UNIT) {
     if (!ctx->graph.valid || ctx->graph.dt != dt || ctx->graph.alpha != alpha)
@@ -616,6 +651,7 @@ int sbx_profile(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha, double *
     ctx->f_dirty = false;
   }
   CK(sbx::prepare_update(ctx, dt, alpha, ctx->stream));
+  if (int rc = ensure_pairs(ctx)) return rc;
   std::vector<cudaEvent_t> ev(3 * n_steps, nullptr);
   int rc = SBX_OK;
   for (auto &e : ev)
@@ -704,7 +740,7 @@ int sbx_adjoint(sbx_ctx *ctx, int64_t n_steps, double dt, int64_t n_rec, const i
   if (!rc) rc = upload(ctx, &d_dat, dat);
   if (!rc) rc = dalloc(ctx, &d_ck, (size_t)(nseg * 2 * nd));
   if (!rc) rc = dalloc(ctx, &d_seg, (size_t)((k + 1) * nd));
-  if (!rc) rc = dalloc(ctx, &d_lam, (size_t)(3 * nd));
+  if (!rc) rc = dalloc(ctx, &d_lam, (size_t)(2 * nd));
   if (!rc) rc = dalloc(ctx, &d_v, (size_t)nd);
   if (!rc) rc = dalloc(ctx, &d_acc, (size_t)ctx->C);
   if (!rc) rc = dalloc(ctx, &d_J, 1);
@@ -731,11 +767,10 @@ int sbx_adjoint(sbx_ctx *ctx, int64_t n_steps, double dt, int64_t n_rec, const i
         ctx->cur ^= 1;
       }
     }
-    CK(cudaMemsetAsync(d_lam, 0, 3 * vb, s));
+    CK(cudaMemsetAsync(d_lam, 0, 2 * vb, s));
     CK(cudaMemsetAsync(d_acc, 0, ctx->C * sizeof(double), s));
     CK(cudaMemsetAsync(d_J, 0, sizeof(double), s));
-    double *lam1 = d_lam, *lam2 = d_lam + nd, *spare = d_lam + 2 * nd;   // lambda_{n+1}, _{n+2}
-    (void)spare;
+    double *lam1 = d_lam, *lam2 = d_lam + nd;   // lambda_{n+1}, lambda_{n+2}
     for (int64_t g = nseg - 1; g >= 0; --g) {
       // recompute U_{gk} .. U_{gk+len} into the segment buffer
       CK(cudaMemcpyAsync(ctx->d_u[0], d_ck + (2 * g) * nd, vb, cudaMemcpyDeviceToDevice, s));
@@ -846,7 +881,14 @@ int read_field(sbx_ctx *ctx, int which, double *out, int64_t len) {
   switch (which) {
     case SBX_U_N: src = ctx->d_u[ctx->cur]; break;
     case SBX_U_NM1: src = ctx->d_u[ctx->cur ^ 1]; break;
-    case SBX_F_INT: src = ctx->d_f; break;
+    case SBX_F_INT:
+      src = ctx->d_f;
+      if (ctx->prec == SBX_PREC_MIXED && ctx->B == 1) {   // float [N][4] -> [3N]
+        CK(sbx::launch_widen_f32(ctx, reinterpret_cast<const float *>(ctx->d_f), ctx->d_fx,
+                                 ctx->stream));
+        src = ctx->d_fx;
+      }
+      break;
     case SBX_MASS: src = ctx->d_mass; need = ctx->ndof; break;
     default: return fail(ctx, SBX_EINVAL, "unknown field");
   }
@@ -871,6 +913,7 @@ int write_field(sbx_ctx *ctx, int which, const double *in, int64_t len) {
   else
     return fail(ctx, SBX_EINVAL, "only U_N and U_NM1 can be written");
   CK(cudaMemcpyAsync(dst, in, len * sizeof(double), cudaMemcpyDefault, ctx->stream));
+  ctx->pair_valid[dst == ctx->d_u[0] ? 0 : 1] = false;
   return SBX_OK;
 }
 

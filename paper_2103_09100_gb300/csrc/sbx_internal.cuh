@@ -45,9 +45,8 @@ struct MeshView {
 constexpr int TC_CLASSES = 3;
 
 // Tensor-core path: a tile of up to 128 cells of one pattern and its unique
-// nodes (tile_nodes[node_off .. node_off + n_nodes)).
-// A tile's record: one contiguous, 16-byte-padded block in global memory,
-// fetched with one bulk copy (see kernels_tc.cu for its layout).
+// nodes.  A tile's record is one contiguous, 16-byte-padded block in global
+// memory, fetched with one bulk copy (layout in kernels_tc.cu).
 struct TcTile {
   int64_t rec_off;    // byte offset of the record
   int32_t rec_bytes;  // multiple of 16
@@ -56,8 +55,6 @@ struct TcTile {
 struct TcPattern {
   int32_t m, kpad, npad, tcols;  // DOFs, K and N padded for the MMA, TMEM columns
   int64_t kc_off;                // K_p hi|lo in canonical layout (float offset)
-  int64_t lidx_off;              // local-index block of the pattern ([n_p][C_p])
-  int64_t cstart, ccount;        // sorted cells of the pattern
 };
 
 struct GraphCache {
@@ -104,7 +101,12 @@ struct sbx_ctx {
   double w_dt = 0.0, w_alpha = 0.0;
   double *d_u[2] = {nullptr, nullptr};
   int cur = 0;                     // d_u[cur] = U_n, d_u[cur ^ 1] = U_{n-1}
-  double *d_f = nullptr;           // R_int - R_ext accumulator
+  double *d_f = nullptr;           // R_int - R_ext accumulator; SBX_PREC_MIXED: float [N][4]
+  double *d_fx = nullptr;          // SBX_PREC_MIXED: d_f widened to FP64 [3N] on demand
+  // SBX_PREC_MIXED: d_u[p] split into FP32 (hi xyz, lo xyz) per node, written
+  // by the update kernel (or by k_split_pairs after a host write)
+  float *d_pair[2] = {nullptr, nullptr};
+  bool pair_valid[2] = {false, false};
   bool f_dirty = false;
   int32_t *d_flags = nullptr;
   int64_t *d_step = nullptr;       // device copy of the step index
@@ -122,7 +124,7 @@ struct sbx_ctx {
   int n_tc_tiles[sbx::TC_CLASSES] = {};
   int tc_kmax[sbx::TC_CLASSES] = {}, tc_nmax[sbx::TC_CLASSES] = {}, tc_tcols[sbx::TC_CLASSES] = {};
   int tc_rec_max[sbx::TC_CLASSES] = {}, tc_nn_max[sbx::TC_CLASSES] = {};
-  int tc_grid[sbx::TC_CLASSES] = {};
+  int tc_grid[sbx::TC_CLASSES] = {}, tc_chunk[sbx::TC_CLASSES] = {};
   size_t tc_smem[sbx::TC_CLASSES] = {};
 
   // batched path (n_rhs > 1): tile records in three classes by pattern size
@@ -190,6 +192,14 @@ cudaError_t launch_force_batch(const sbx_ctx *ctx, const double *u, double *f, d
                                cudaStream_t s);
 cudaError_t launch_update_batch(const sbx_ctx *ctx, const double *uc, double *up, double *f,
                                 double dt, double alpha, int zero_f, cudaStream_t s);
-cudaError_t launch_force_tc(const sbx_ctx *ctx, const double *u, double *f, double dt,
+// Mixed form: f is float [N][4] (x, y, z, unused) in the d_f allocation;
+// U_n enters the force kernel as its (hi, lo) pairs, float [N][6].
+cudaError_t launch_force_tc(const sbx_ctx *ctx, const float *pairs, float *f4, double dt,
                             cudaStream_t s);
+cudaError_t launch_update_f32(const sbx_ctx *ctx, const double *uc, double *up, float *f4,
+                              float *pairs_out, double dt, double alpha, int zero_f,
+                              cudaStream_t s);
+cudaError_t launch_split_pairs(const sbx_ctx *ctx, const double *u, float *pairs, cudaStream_t s);
+// out[3 i + d] = f4[4 i + d] (FP64)
+cudaError_t launch_widen_f32(const sbx_ctx *ctx, const float *f4, double *out, cudaStream_t s);
 }  // namespace sbx

@@ -68,3 +68,24 @@ def test_mixed_full_size_cavity_200_steps():
     e = rel(S.field(L.SBX_U_N), u)
     print("cavity mixed 200-step rel error %.3e" % e)
     assert e < 1e-5
+
+
+def test_mixed_receiver_cube_force_and_100_steps():
+    # ~100k cells: full 128-cell tiles of the 8-node cell (the unrolled
+    # path) with a ragged last tile, and the general path for the rest
+    m = og.config_receiver_cube()
+    P = cdm.make_problem(m)
+    S = Solver.from_mesh(m, precision="mixed", dt=P.dt)
+    u0 = np.random.default_rng(5).standard_normal(m.n_dof)
+    u0[P.fixed] = 0
+    S.initial(u0)
+    S.step(1)
+    ref = cdm.apply_K(P, u0) - cdm.external_force(P, 0)
+    assert rel(S.field(L.SBX_F_INT), ref) < 1e-5
+    u, up = cdm.initial_state(P, u0)
+    S.initial(u0)
+    S.step(100)
+    u, up, _, _ = cdm.run(P, 100, u, up, threads=16)
+    e = rel(S.field(L.SBX_U_N), u)
+    print("receiver cube mixed 100-step rel error %.3e" % e)
+    assert e < 1e-5
