@@ -116,7 +116,9 @@ void free_mesh(sbx_ctx *ctx) {
   dfree(ctx->d_tiles_simt);
   dfree(ctx->d_load_dof); dfree(ctx->d_load_amp); dfree(ctx->d_load_t1); dfree(ctx->d_load_ncyc);
   dfree(ctx->d_load_kind);
-  dfree(ctx->d_tc_pat); dfree(ctx->d_tc_K); dfree(ctx->d_tc_rec);
+  dfree(ctx->d_tc_K); dfree(ctx->d_tc_rec); dfree(ctx->d_gen_tiles); dfree(ctx->d_gen_K);
+  dfree(ctx->d_gen_koff);
+  ctx->n_gen_tiles = 0;
   dfree(ctx->d_b_rec);
   for (int c = 0; c < 3; ++c) {
     dfree(ctx->d_b_tiles[c]);
@@ -838,10 +840,8 @@ int sbx_query(sbx_ctx *ctx, int what, int64_t *out) {
       tiles += (int64_t)ctx->n_b_tiles[c] * (ctx->B / 32);
     }
   } else if (ctx->prec == SBX_PREC_MIXED) {
-    for (int c = 0; c < sbx::TC_CLASSES; ++c) {
-      launches += ctx->n_tc_tiles[c] > 0;
-      tiles += ctx->n_tc_tiles[c];
-    }
+    launches = (ctx->n_tc_tiles[0] > 0) + (ctx->n_gen_tiles > 0);
+    tiles = ctx->n_tc_tiles[0] + ctx->n_gen_tiles;
   } else {
     launches = ctx->n_tiles_simt > 0;
     tiles = ctx->n_tiles_simt;

@@ -42,7 +42,7 @@ struct MeshView {
   const double *scale;        // s_e = E_e h_e per sorted cell
 };
 
-constexpr int TC_CLASSES = 3;
+constexpr int TC_CLASSES = 1;
 
 // Tensor-core path: a tile of up to 128 cells of one pattern and its unique
 // nodes.  A tile's record is one contiguous, 16-byte-padded block in global
@@ -51,10 +51,6 @@ struct TcTile {
   int64_t rec_off;    // byte offset of the record
   int32_t rec_bytes;  // multiple of 16
   int32_t pat;
-};
-struct TcPattern {
-  int32_t m, kpad, npad, tcols;  // DOFs, K and N padded for the MMA, TMEM columns
-  int64_t kc_off;                // K_p hi|lo in canonical layout (float offset)
 };
 
 struct GraphCache {
@@ -115,17 +111,20 @@ struct sbx_ctx {
   int n_tiles_simt = 0;
   int max_m = 0;
 
-  // tensor-core path (SBX_PREC_MIXED); tiles in launch classes by the
-  // shared memory they need
-  sbx::TcPattern *d_tc_pat = nullptr;
-  float *d_tc_K = nullptr;
+  // mixed path (SBX_PREC_MIXED): tensor-core tiles of the 8-node cell and
+  // 32-cell SIMT tiles of the other patterns
+  float *d_tc_K = nullptr;         // K_p of the 8-node cell, TF32 hi | lo, canonical layout
   uint8_t *d_tc_rec = nullptr;     // tile records
   sbx::TcTile *d_tc_tiles[sbx::TC_CLASSES] = {};
   int n_tc_tiles[sbx::TC_CLASSES] = {};
-  int tc_kmax[sbx::TC_CLASSES] = {}, tc_nmax[sbx::TC_CLASSES] = {}, tc_tcols[sbx::TC_CLASSES] = {};
   int tc_rec_max[sbx::TC_CLASSES] = {}, tc_nn_max[sbx::TC_CLASSES] = {};
-  int tc_grid[sbx::TC_CLASSES] = {}, tc_chunk[sbx::TC_CLASSES] = {};
+  int tc_grid[sbx::TC_CLASSES] = {};
   size_t tc_smem[sbx::TC_CLASSES] = {};
+  sbx::Tile *d_gen_tiles = nullptr;
+  float *d_gen_K = nullptr;        // FP32 K_p of those patterns, rows padded to a multiple of 4
+  int64_t *d_gen_koff = nullptr;
+  int n_gen_tiles = 0;
+  size_t gen_smem = 0;
 
   // batched path (n_rhs > 1): tile records in three classes by pattern size
   uint8_t *d_b_rec = nullptr;
