@@ -625,9 +625,10 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
   // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per
-  // CTA), at most 4 (registers, tensor memory)
+  // CTA), at most 4 (registers, tensor memory); 3 when k_force_gen runs
+  // beside it
   int per_sm = (int)((228u * 1024u) / (ctx->tc_smem[0] + 1024u));
-  per_sm = std::max(1, std::min(per_sm, 4));
+  per_sm = std::max(1, std::min(per_sm, gen.empty() ? 4 : 3));
   ctx->tc_grid[0] = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)nsm * per_sm));
   if (ctx->tc_smem[0] > 227u * 1024u) {
     err = "tensor-core tile needs more than 227 KB of shared memory";
@@ -651,20 +652,37 @@ cudaError_t prepare_tc_kernels() {
                               (int)gen_smem(78));
 }
 
+// The two kernels run side by side: the tensor-core kernel's persistent
+// grid leaves room on every SM for one k_force_gen CTA, which runs on the
+// context's second stream (fork and join by events; also under capture).
 cudaError_t launch_force_tc(const sbx_ctx *ctx, const float *pairs, float *f4, double dt,
                             cudaStream_t s) {
   LoadTable L = ctx->loads();   // added by CTA 0 of the first launch only
+  const bool both = ctx->n_tc_tiles[0] > 0 && ctx->n_gen_tiles > 0;
+  cudaError_t e;
+  if (both) {
+    if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0)) != cudaSuccess) return e;
+  }
   if (ctx->n_tc_tiles[0] > 0) {
     k_force_tc<<<ctx->tc_grid[0], TC_THREADS, ctx->tc_smem[0], s>>>(
         ctx->d_tc_tiles[0], ctx->n_tc_tiles[0], ctx->d_tc_rec, ctx->d_tc_K, pairs, f4, L,
         ctx->d_step, dt, ctx->d_flags, ctx->tc_rec_max[0], ctx->tc_nn_max[0]);
     L.n = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (ctx->n_gen_tiles > 0)
-    k_force_gen<<<ctx->n_gen_tiles, 256, ctx->gen_smem, s>>>(ctx->d_gen_tiles, ctx->view(),
-                                                             ctx->d_gen_K, ctx->d_gen_koff,
-                                                             pairs, f4, L, ctx->d_step, dt);
-  return cudaGetLastError();
+  if (ctx->n_gen_tiles > 0) {
+    cudaStream_t sg = both ? ctx->side : s;
+    k_force_gen<<<ctx->n_gen_tiles, 256, ctx->gen_smem, sg>>>(ctx->d_gen_tiles, ctx->view(),
+                                                              ctx->d_gen_K, ctx->d_gen_koff,
+                                                              pairs, f4, L, ctx->d_step, dt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (both) {
+    if ((e = cudaEventRecord(ctx->ev_join, ctx->side)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, ctx->ev_join, 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace sbx

@@ -250,6 +250,13 @@ int sbx_create(sbx_ctx **out, int device, void *cuda_stream) {
     }
     ctx->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    sbx_destroy(ctx);
+    return SBX_ECUDA;
+  }
   if (sbx::prepare_kernels() != cudaSuccess || sbx::prepare_tc_kernels() != cudaSuccess ||
       sbx::prepare_batch_kernels() != cudaSuccess || sbx::prepare_adjoint_kernels() != cudaSuccess) {
     cudaGetLastError();
@@ -274,6 +281,12 @@ int sbx_destroy(sbx_ctx *ctx) {
   free_patterns(ctx);
   dfree(ctx->d_flags);
   dfree(ctx->d_step);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return SBX_OK;

@@ -65,6 +65,10 @@ struct GraphCache {
 struct sbx_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  // second stream for a force kernel that runs beside the first (forked
+  // from and joined back into `stream` with the two events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool own_stream = false;
   std::string err;
 
