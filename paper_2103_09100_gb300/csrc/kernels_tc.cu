@@ -17,9 +17,11 @@
 //                engine, completion on an mbarrier) and tile i+1's node
 //                pairs by per-thread cp.async while tile i is computed.
 //                A (128 x 24) = the cells' differences rounded to TF32 hi +
-//                lo;  D (TMEM) = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
-//                with B = K_p split the same way (tcgen05.mma kind::tf32 by
-//                one thread, completion by tcgen05.commit -> mbarrier);
+//                lo, written to tensor memory by tcgen05.st (row = cell =
+//                TMEM lane);  D (TMEM) = A_hi B_hi^T + A_hi B_lo^T + A_lo
+//                B_hi^T with B = K_p split the same way in shared memory
+//                (tcgen05.mma kind::tf32 by one thread, completion by
+//                tcgen05.commit -> mbarrier);
 //                tcgen05.ld D (row = cell) times E_e h_e into shared memory;
 //                each node sums its incidences (per-tile list) in FP32.
 //   k_force_gen  every other pattern and op (hanging-node cells: a few per
@@ -28,9 +30,10 @@
 //                the cell frame (Sec. 3.2.2), one vector reduction per
 //                (cell, node).
 //
-// Tensor-core operands use the canonical no-swizzle K-major layout: 8-row x
-// 16-byte core matrices, row groups nK * 128 B apart, K groups 128 B apart
-// within a row group (LBO = 128 B, SBO = nK * 128 B).
+// B uses the canonical no-swizzle K-major layout: 8-row x 16-byte core
+// matrices, row groups nK * 128 B apart, K groups 128 B apart within a row
+// group (LBO = 128 B, SBO = nK * 128 B).  TMEM columns: D 0..31, A_hi
+// 32..55, A_lo 64..87.
 //
 // Tile record of k_force_tc (every part padded to 16 bytes):
 //   int32 {pat, ncell, nn, 0}          header
@@ -57,8 +60,9 @@ namespace {
 
 constexpr int TC_THREADS = 256;
 constexpr uint32_t WAIT_POLLS = 1u << 22;
-constexpr int FAST_NN_CAP = 272;   // unique nodes per tile: keeps 4 CTAs per SM
-constexpr int KM = 24, KPAD = 24, NPAD = 32, NK = KPAD / 4, TCOLS = 32;   // 8-node cell
+constexpr int FAST_NN_CAP = 320;   // unique nodes per tile: keeps 4 CTAs per SM
+constexpr int KM = 24, KPAD = 24, NPAD = 32, NK = KPAD / 4;   // 8-node cell
+constexpr int TCOLS = 128, COL_AHI = 32, COL_ALO = 64;         // TMEM columns
 constexpr int GEN_TILE = 32;       // cells per k_force_gen CTA
 
 __host__ __device__ inline uint32_t a16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -80,15 +84,15 @@ __host__ __device__ inline RecLayout rec_layout(int ncell, int nn) {
 }
 
 struct SmemLayout {
-  uint32_t B, A, stage[2], u_off, total;
+  uint32_t B, F, stage[2], u_off, total;
 };
-// A (hi | lo) also holds F = E h D after the MMA as float4 [8][128] (slot,
-// cell).  Each stage: a record, then the tile's node pairs (24 B per node).
+// F = E h D as float4 [8][128] (slot, cell).  Each stage: a record, then the
+// tile's node pairs (24 B per node).
 __host__ __device__ inline SmemLayout smem_layout(int rec_max, int nn_max) {
   SmemLayout L;
   uint32_t o = 128;                                    // 3 mbarriers + TMEM address
   L.B = o;   o = a128(o + 2u * NPAD * KPAD * 4u);
-  L.A = o;   o = a128(o + 2u * 128u * KPAD * 4u);
+  L.F = o;   o = a128(o + 8u * 128u * 16u);
   L.u_off = a16((uint32_t)rec_max);
   const uint32_t st = a128(L.u_off + 24u * (uint32_t)nn_max);
   L.stage[0] = o; o += st;
@@ -115,11 +119,6 @@ __device__ inline Stage stage_view(const unsigned char *base, uint32_t u_off) {
   S.inc = reinterpret_cast<const uint16_t *>(base + R.inc);
   S.u = reinterpret_cast<const float *>(base + u_off);
   return S;
-}
-
-// Float offset of A(c, col) in the canonical K-major layout.
-__device__ __forceinline__ int a_off(int c, int col) {
-  return (c >> 3) * NK * 32 + (c & 7) * 4 + (col >> 2) * 32 + (col & 3);
 }
 
 __device__ __forceinline__ void red_add_v4(float *addr, float x, float y, float z) {
@@ -163,7 +162,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
   uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [0] MMA, [1], [2] records
   uint32_t *taddr_s = reinterpret_cast<uint32_t *>(smem + 32);
   float *Bs = reinterpret_cast<float *>(smem + SL.B);
-  float *Ahi = reinterpret_cast<float *>(smem + SL.A), *Alo = Ahi + 128 * KPAD;
+  float4 *F4 = reinterpret_cast<float4 *>(smem + SL.F);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int G = gridDim.x;
   const uint32_t mb_mma = tc::smem_addr(&mbar[0]);
@@ -191,8 +190,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
   const uint32_t taddr = *taddr_s;
 
   auto stage_base = [&](int s) { return smem + (s ? SL.stage[1] : SL.stage[0]); };
-  auto issue_record = [&](int s, int tile) {   // thread 0 only
-    const TcTile T = tiles[tile];
+  auto issue_record = [&](int s, const TcTile &T) {   // thread 0 only
     tc::fence_proxy_async_smem();
     const uint32_t mb = mb_rec0 + 8u * (uint32_t)s;
     tc::mbar_arrive_expect_tx(mb, (uint32_t)T.rec_bytes);
@@ -217,8 +215,8 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
   int tile = blockIdx.x;
   if (tile < ntiles) {
     if (tid == 0) {
-      issue_record(0, tile);
-      if (tile + G < ntiles) issue_record(1, tile + G);
+      issue_record(0, tiles[tile]);
+      if (tile + G < ntiles) issue_record(1, tiles[tile + G]);
     }
     pend = 1u | (tile + G < ntiles ? 2u : 0u);
     ok = __syncthreads_and(tc::mbar_wait_bounded(mb_rec0, ph_rec & 1u, WAIT_POLLS));
@@ -234,62 +232,68 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
   for (int i = 0; ok && tile < ntiles; ++i, tile += G) {
     const int s = i & 1;
     const uint32_t so = (uint32_t)(s ^ 1);
-    tc::cp_async_wait_all();
-    __syncthreads();
     const int next = tile + G;
+    TcTile ahead;   // descriptor of tile i + 2 (thread 0), fetched early
+    if (tid == 0 && next + G < ntiles) ahead = tiles[next + G];
+    // this tile's node pairs (own cp.async) and the next tile's record
+    tc::cp_async_wait_all();
+    bool got = true;
+    if (next < ntiles) got = tc::mbar_wait_bounded(mb_rec0 + 8u * so, (ph_rec >> so) & 1u, WAIT_POLLS);
+    ok = __syncthreads_and(got);
+    if (!ok) break;
     if (next < ntiles) {
-      ok = __syncthreads_and(
-          tc::mbar_wait_bounded(mb_rec0 + 8u * so, (ph_rec >> so) & 1u, WAIT_POLLS));
-      if (!ok) break;
       ph_rec ^= 1u << so;
       pend &= ~(1u << so);
       issue_gather(s ^ 1);
     }
     const Stage S = stage_view(stage_base(s), SL.u_off);
     const int ncell = S.hdr[1], nn = S.hdr[2];
-    // A rows: differences to slot 0, TF32 hi + lo, three float4 per operand
-    if (fc < ncell) {
-      const uint4 L = *reinterpret_cast<const uint4 *>(S.lid + 8 * fc);
-      const uint32_t lw0 = fh ? L.z : L.x, lw1 = fh ? L.w : L.y;
-      const float *ref = S.u + 6 * (L.x & 0xFFFFu);
+    // A rows: differences to slot 0, TF32 hi + lo, into TMEM columns
+    // COL_AHI / COL_ALO + 12 h .. + 11 of lane = cell (rows past ncell: 0)
+    {
       float vh[12], vl[12];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const uint32_t lk = ((t < 2 ? lw0 : lw1) >> (16 * (t & 1))) & 0xFFFFu;
-        float d[3];
-        node_diff(S.u + 6 * lk, ref, d[0], d[1], d[2]);
+      for (int q = 0; q < 12; ++q) vh[q] = vl[q] = 0.0f;
+      if (fc < ncell) {
+        const uint4 L = *reinterpret_cast<const uint4 *>(S.lid + 8 * fc);
+        const uint32_t lw0 = fh ? L.z : L.x, lw1 = fh ? L.w : L.y;
+        const float *ref = S.u + 6 * (L.x & 0xFFFFu);
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          vh[3 * t + r] = tc::to_tf32(d[r]);
-          vl[3 * t + r] = tc::to_tf32(d[r] - vh[3 * t + r]);
+        for (int t = 0; t < 4; ++t) {
+          const uint32_t lk = ((t < 2 ? lw0 : lw1) >> (16 * (t & 1))) & 0xFFFFu;
+          float d[3];
+          node_diff(S.u + 6 * lk, ref, d[0], d[1], d[2]);
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            vh[3 * t + r] = tc::to_tf32(d[r]);
+            vl[3 * t + r] = tc::to_tf32(d[r] - vh[3 * t + r]);
+          }
         }
       }
-#pragma unroll
-      for (int g = 0; g < 3; ++g) {
-        const int o = a_off(fc, 12 * fh + 4 * g);
-        *reinterpret_cast<float4 *>(Ahi + o) =
-            make_float4(vh[4 * g], vh[4 * g + 1], vh[4 * g + 2], vh[4 * g + 3]);
-        *reinterpret_cast<float4 *>(Alo + o) =
-            make_float4(vl[4 * g], vl[4 * g + 1], vl[4 * g + 2], vl[4 * g + 3]);
-      }
+      const uint32_t col = (uint32_t)(12 * fh);
+      const float h8[8] = {vh[0], vh[1], vh[2], vh[3], vh[4], vh[5], vh[6], vh[7]};
+      const float l8[8] = {vl[0], vl[1], vl[2], vl[3], vl[4], vl[5], vl[6], vl[7]};
+      tc::tmem_st8(taddr + lane_base + COL_AHI + col, h8);
+      tc::tmem_st4(taddr + lane_base + COL_AHI + col + 8u, vh[8], vh[9], vh[10], vh[11]);
+      tc::tmem_st8(taddr + lane_base + COL_ALO + col, l8);
+      tc::tmem_st4(taddr + lane_base + COL_ALO + col + 8u, vl[8], vl[9], vl[10], vl[11]);
+      tc::tmem_st_wait();
     }
-    tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     if (tid == 0) {
       const uint32_t idesc = tc::idesc_tf32(128, NPAD);
-      const uint32_t a_hi = tc::smem_addr(Ahi), a_lo = tc::smem_addr(Alo);
       const uint32_t b_hi = tc::smem_addr(Bs), b_lo = tc::smem_addr(Bs + NPAD * KPAD);
       const uint32_t sbo = (uint32_t)NK * 128u;
 #pragma unroll
       for (int ks = 0; ks < KPAD / 8; ++ks) {
         const uint32_t o = (uint32_t)ks * 256u;
-        const uint64_t ah = tc::smem_desc(a_hi + o, 128, sbo), al = tc::smem_desc(a_lo + o, 128, sbo);
         const uint64_t bh = tc::smem_desc(b_hi + o, 128, sbo), bl = tc::smem_desc(b_lo + o, 128, sbo);
-        tc::mma_tf32(taddr, ah, bh, idesc, ks > 0 ? 1u : 0u);
-        tc::mma_tf32(taddr, ah, bl, idesc, 1u);
-        tc::mma_tf32(taddr, al, bh, idesc, 1u);
+        const uint32_t ah = taddr + COL_AHI + 8u * ks, al = taddr + COL_ALO + 8u * ks;
+        tc::mma_tf32_ta(taddr, ah, bh, idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32_ta(taddr, ah, bl, idesc, 1u);
+        tc::mma_tf32_ta(taddr, al, bh, idesc, 1u);
       }
       tc::mma_commit(mb_mma);
     }
@@ -298,7 +302,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
     if (!ok) break;
     ph_mma ^= 1u;
     // epilogue: warps w and w + 4 read TMEM lanes 32 (w % 4) .. + 31, columns
-    // 12 h .. 12 h + 11; F4[slot][cell] = E h D overwrites A
+    // 12 h .. 12 h + 11; F4[slot][cell] = E h D
     {
       float v[12];
       {
@@ -316,7 +320,6 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
       }
       if (fc < ncell) {
         const float sc = S.scale[fc];
-        float4 *F4 = reinterpret_cast<float4 *>(Ahi);
 #pragma unroll
         for (int t = 0; t < 4; ++t)
           F4[(4 * fh + t) * 128 + fc] =
@@ -327,7 +330,6 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
     __syncthreads();
     // node sums over the incidences (cell, slot): at most 8 per node
     {
-      const float4 *F4 = reinterpret_cast<const float4 *>(Ahi);
       for (int q = tid; q < nn; q += TC_THREADS) {
         float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
         const int j0 = S.off[q], nj = S.off[q + 1] - j0;
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
     }
     __syncthreads();   // stage s and F are free
     if (next + G < ntiles) {
-      if (tid == 0) issue_record(s, next + G);
+      if (tid == 0) issue_record(s, ahead);
       pend |= 1u << s;
     }
   }
