@@ -41,6 +41,10 @@ UNIT = "DOF*steps/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA pipe of GB300: 2 DFMA / clk / SM x 152 SMs x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one force launch pair on the cavity cube, from
+# the ncu capture summarised in profiles/k_force_tc_mixed_cavity_cube.md
+# (k_force_tc 96.7 MB + k_force_gen 13.1 MB); valid for that kernel version
+FORCE_TRAFFIC_MIXED = 109.8e6
 
 
 def dist_env():
@@ -239,10 +243,12 @@ def main():
                 "peak_source": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)"}
     else:
         ach = bytes_force / t_force / 1e9
+        mixed = args.precision == "mixed"
         roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": None,
-                "kernel": "k_force_tc (all launch classes of one step)" if args.precision == "mixed"
-                else "k_force_simt<float>", "peak_source": "hbm_gbs " + pk_src}
+                "frac": ach / pk["hbm_gbs"],
+                "traffic": FORCE_TRAFFIC_MIXED if mixed else None,
+                "kernel": "force launch pair k_force_tc + k_force_gen (concurrent streams)"
+                if mixed else "k_force_simt<float>", "peak_source": "hbm_gbs " + pk_src}
         if args.precision == "mixed":
             roof["tensor_tflops_tf32"] = 3 * flops / t_force / 1e12
     roof.update({"algorithmic_bytes_per_launch": bytes_force, "force_ms": t_force * 1e3,
