@@ -236,6 +236,56 @@ int sbx_adjoint(sbx_ctx *ctx, int64_t n_steps, double dt, int64_t n_rec,
                 double *misfit_out, double *grad_E_out);
 
 /*
+ * Split step, for a caller that must act between the internal force and the
+ * update -- the interface sum of the node-cut partition (Sec. 4: each GPU
+ * holds the cells of its part and the nodes they touch; the partial forces
+ * of the nodes on a cut are summed over the parts before every update) or
+ * any other force added from outside.  One step of step_n equals
+ *   sbx_force(ctx, dt); <modify f>; sbx_update(ctx, dt, alpha);
+ * sbx_force: f = R_int(U_n) - R_ext(t_n) into the force buffer (Eq. Rintep
+ *   and the load term).  sbx_update: Eq. DnMdiag with that f, U_{n+1}
+ *   replaces U_{n-1}, the step index advances and f is cleared.  Both are
+ *   asynchronous.  Calling sbx_update without a preceding sbx_force, or
+ *   sbx_force twice, is SBX_ESTATE.
+ *   Errors: SBX_ESTATE, SBX_EINVAL (dt, alpha), SBX_ECUDA.
+ */
+int sbx_force(sbx_ctx *ctx, double dt);
+int sbx_update(sbx_ctx *ctx, double dt, double alpha);
+
+/*
+ * sbx_field_ptr: device address and layout of a field the library owns, for
+ * in-place access on the context's stream (e.g. a collective between
+ * sbx_force and sbx_update).  which = SBX_U_N, SBX_U_NM1, SBX_F_INT or
+ * SBX_MASS.  *layout:
+ *   SBX_LAYOUT_F64_DOF    double per DOF (entry 3 node + d, times B load
+ *                         cases as in read_field); *len = 3 N B (3 N for
+ *                         SBX_MASS)
+ *   SBX_LAYOUT_F32_NODE4  float [N][4] (x, y, z, unused): SBX_F_INT of
+ *                         SBX_PREC_MIXED meshes; *len = 4 N
+ * The address stays valid until the next mesh_upload or sbx_destroy; the
+ * buffers behind SBX_U_N / SBX_U_NM1 swap roles every step, so ask again
+ * after each step.  After writing U_n or U_{n-1} through the pointer, call
+ * sbx_touch (below).
+ *   Errors: SBX_ESTATE (no mesh), SBX_EINVAL (which, NULL outputs).
+ */
+#define SBX_LAYOUT_F64_DOF   0
+#define SBX_LAYOUT_F32_NODE4 1
+int sbx_field_ptr(sbx_ctx *ctx, int which, void **ptr, int64_t *len, int *layout);
+
+/* sbx_touch: tell the library that U_n was changed through sbx_field_ptr
+ * (the mixed form re-derives its FP32 (hi, lo) split of U_n). */
+int sbx_touch(sbx_ctx *ctx);
+
+/*
+ * sbx_set_mass: replace the lumped diagonal mass M_diag[3N] (Sec. 3.3) --
+ * e.g. by the sum over all parts of a node-cut partition, whose interface
+ * nodes receive mass from cells on several GPUs.  Values > 0; M^-1 stays 0
+ * on the Dirichlet DOFs.
+ *   Errors: SBX_ESTATE (no mesh), SBX_EINVAL (values, NULL).
+ */
+int sbx_set_mass(sbx_ctx *ctx, const double *mass);
+
+/*
  * sbx_query: diagnostics about the uploaded mesh and the launch plan.
  *   what = SBX_Q_KERNELS_PER_STEP  kernel launches per step (force + update)
  *          SBX_Q_FORCE_LAUNCHES    force-kernel launches per step

@@ -26,7 +26,9 @@ STATUS_NAMES = {0: "SBX_OK", 1: "SBX_EINVAL", 2: "SBX_ENOMEM", 3: "SBX_ECUDA",
 EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patterns",
            "mesh_upload", "set_load", "set_initial", "step_n", "sbx_get_step", "sbx_set_step",
            "read_field", "write_field", "sbx_profile", "sbx_query", "sbx_step_static",
-           "set_modulus", "sbx_adjoint"]
+           "set_modulus", "sbx_adjoint", "sbx_force", "sbx_update", "sbx_field_ptr", "sbx_touch",
+           "sbx_set_mass"]
+SBX_LAYOUT_F64_DOF, SBX_LAYOUT_F32_NODE4 = 0, 1
 SBX_Q_KERNELS_PER_STEP, SBX_Q_FORCE_LAUNCHES, SBX_Q_TILES = 0, 1, 2
 SBX_STATIC_MAX_DOF = 4 * 1024 * 1024
 SBX_STATIC_MAX_PATTERNS = 144
@@ -68,6 +70,11 @@ def load(path: str = LIB_PATH):
         "sbx_query": [vp, i32, C.POINTER(i64)],
         "set_modulus": [vp, vp],
         "sbx_adjoint": [vp, i64, dbl, i64, vp, vp, i64, C.POINTER(dbl), vp],
+        "sbx_force": [vp, dbl],
+        "sbx_update": [vp, dbl, dbl],
+        "sbx_field_ptr": [vp, i32, C.POINTER(vp), C.POINTER(i64), C.POINTER(i32)],
+        "sbx_touch": [vp],
+        "sbx_set_mass": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -161,6 +168,29 @@ def sbx_adjoint(ctx, n_steps, dt, rec_dof, data, ckpt_every, grad_out):
                                    _ptr(rec_dof, np.int64), _ptr(data, np.float64),
                                    int(ckpt_every), C.byref(J), _ptr(grad_out, np.float64)))
     return J.value
+
+
+def sbx_force(ctx, dt):
+    _check(ctx, load().sbx_force(ctx, float(dt)))
+
+
+def sbx_update(ctx, dt, alpha=0.0):
+    _check(ctx, load().sbx_update(ctx, float(dt), float(alpha)))
+
+
+def sbx_field_ptr(ctx, which):
+    """(device address, element count, layout) of a library-owned field."""
+    p, n, lay = C.c_void_p(), C.c_int64(), C.c_int()
+    _check(ctx, load().sbx_field_ptr(ctx, int(which), C.byref(p), C.byref(n), C.byref(lay)))
+    return p.value, n.value, lay.value
+
+
+def sbx_touch(ctx):
+    _check(ctx, load().sbx_touch(ctx))
+
+
+def sbx_set_mass(ctx, mass):
+    _check(ctx, load().sbx_set_mass(ctx, _ptr(mass, np.float64)))
 
 
 def sbx_query(ctx, what) -> int:

@@ -503,6 +503,8 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   ctx->N = n_nodes;
   ctx->C = n_cells;
   ctx->ndof = ndof;
+  ctx->h_fixed = fixed;
+  ctx->f_pending = false;
   ctx->B = n_rhs;
   ctx->prec = precision_mode;
   ctx->pat_cstart = start;
@@ -613,7 +615,7 @@ int set_initial(sbx_ctx *ctx, const double *u0, const double *v0, double dt, dou
   CK(cudaMemsetAsync(ctx->d_f, 0, bytes, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t), ctx->stream));
   ctx->step = 0;
-  ctx->f_dirty = false;
+  ctx->f_dirty = ctx->f_pending = false;
   return SBX_OK;
 }
 
@@ -626,9 +628,9 @@ int step_n(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha) {
     return fail(ctx, SBX_EINVAL, "need n_steps >= 0, dt > 0, alpha >= 0");
   if (n_steps == 0) return SBX_OK;
   const size_t bytes = ctx->ndof * ctx->B * sizeof(double);
-  if (ctx->f_dirty) {
+  if (ctx->f_dirty || ctx->f_pending) {
     CK(cudaMemsetAsync(ctx->d_f, 0, bytes, ctx->stream));
-    ctx->f_dirty = false;
+    ctx->f_dirty = ctx->f_pending = false;
   }
   CK(sbx::prepare_update(ctx, dt, alpha, ctx->stream));
   if (int rc = ensure_pairs(ctx)) return rc;
@@ -841,6 +843,89 @@ int sbx_adjoint(sbx_ctx *ctx, int64_t n_steps, double dt, int64_t n_rec, const i
   ctx->step = 0;
   release();
   return rc;
+}
+
+int sbx_force(sbx_ctx *ctx, double dt) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before sbx_force");
+  if (ctx->f_pending) return fail(ctx, SBX_ESTATE, "sbx_force twice without sbx_update");
+  if (!(dt > 0) || !isfinite(dt)) return fail(ctx, SBX_EINVAL, "dt must be > 0");
+  if (ctx->f_dirty) {
+    CK(cudaMemsetAsync(ctx->d_f, 0, ctx->ndof * ctx->B * sizeof(double), ctx->stream));
+    ctx->f_dirty = false;
+  }
+  if (int rc = ensure_pairs(ctx)) return rc;
+  if (int rc = force(ctx, ctx->d_u[ctx->cur], ctx->d_f, dt)) return rc;
+  ctx->f_pending = true;
+  return SBX_OK;
+}
+
+int sbx_update(sbx_ctx *ctx, double dt, double alpha) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before sbx_update");
+  if (!ctx->f_pending) return fail(ctx, SBX_ESTATE, "sbx_update needs a preceding sbx_force");
+  if (!(dt > 0) || !(alpha >= 0) || !isfinite(dt) || !isfinite(alpha))
+    return fail(ctx, SBX_EINVAL, "need dt > 0, alpha >= 0");
+  CK(sbx::prepare_update(ctx, dt, alpha, ctx->stream));
+  if (int rc = update(ctx, ctx->d_u[ctx->cur], ctx->d_u[ctx->cur ^ 1], dt, alpha, 1)) return rc;
+  ctx->cur ^= 1;
+  ctx->step += 1;
+  ctx->f_pending = false;
+  return SBX_OK;
+}
+
+int sbx_field_ptr(sbx_ctx *ctx, int which, void **ptr, int64_t *len, int *layout) {
+  if (!ctx || !ptr || !len || !layout) return SBX_EINVAL;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
+  *layout = SBX_LAYOUT_F64_DOF;
+  *len = ctx->ndof * ctx->B;
+  switch (which) {
+    case SBX_U_N: *ptr = ctx->d_u[ctx->cur]; break;
+    case SBX_U_NM1: *ptr = ctx->d_u[ctx->cur ^ 1]; break;
+    case SBX_F_INT:
+      *ptr = ctx->d_f;
+      if (ctx->prec == SBX_PREC_MIXED && ctx->B == 1) {
+        *layout = SBX_LAYOUT_F32_NODE4;
+        *len = 4 * ctx->N;
+      }
+      break;
+    case SBX_MASS: *ptr = ctx->d_mass; *len = ctx->ndof; break;
+    default: return fail(ctx, SBX_EINVAL, "unknown field");
+  }
+  return SBX_OK;
+}
+
+int sbx_touch(sbx_ctx *ctx) {
+  if (!ctx) return SBX_EINVAL;
+  ctx->pair_valid[0] = ctx->pair_valid[1] = false;
+  return SBX_OK;
+}
+
+int sbx_set_mass(sbx_ctx *ctx, const double *mass) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
+  std::vector<double> m;
+  if (int rc = fetch_vec(ctx, m, mass, (size_t)ctx->ndof)) return rc;
+  std::vector<double> minv(ctx->ndof);
+  for (int64_t d = 0; d < ctx->ndof; ++d) {
+    if (!(m[d] > 0) || !isfinite(m[d])) return fail(ctx, SBX_EINVAL, "mass must be positive and finite");
+    minv[d] = 1.0 / m[d];
+  }
+  for (int64_t d : ctx->h_fixed) minv[d] = 0.0;
+  CK(cudaMemcpyAsync(ctx->d_mass, m.data(), m.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_minv, minv.data(), minv.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->w_valid = false;
+  return SBX_OK;
 }
 
 int sbx_query(sbx_ctx *ctx, int what, int64_t *out) {

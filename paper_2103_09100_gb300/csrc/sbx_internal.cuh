@@ -108,6 +108,8 @@ struct sbx_ctx {
   float *d_pair[2] = {nullptr, nullptr};
   bool pair_valid[2] = {false, false};
   bool f_dirty = false;
+  bool f_pending = false;          // sbx_force done, sbx_update not yet
+  std::vector<int64_t> h_fixed;    // Dirichlet DOFs (M^-1 = 0)
   int32_t *d_flags = nullptr;
   int64_t *d_step = nullptr;       // device copy of the step index
   int64_t step = 0;

@@ -1,0 +1,211 @@
+"""Node-cut multi-GPU stepping (Sec. 4): one ``Solver`` per part, the
+partial internal forces of the cut nodes summed every step.
+
+``NodeCutSolver`` is one part on one GPU (one rank).  It splits every step
+into ``sbx_force`` -> interface sum -> ``sbx_update`` through the C ABI and
+reaches the library's force buffer in place (``sbx_field_ptr``), so the sum
+runs on the device on the library's stream (NCCL ``all_reduce`` under
+``torch.distributed``).  ``step_distributed`` drives any engine with the
+same four methods (``force`` -> True when it computed a new partial force,
+``pack_force``, ``unpack_force``, ``update``) over ``torch.distributed``;
+``step_together`` drives several engines held by one process (the parts
+then take turns on one device).
+
+Set-up: the lumped mass of the cut nodes is summed once (``sbx_set_mass``),
+dt is the minimum of the parts' critical steps times ``dt_factor``, and the
+start-up of Eq. D0 uses the summed initial force: after ``set_initial`` the
+part evaluates f_0 = K U_0 - R_ext(0), sums it, rewrites U_-1 = U_0 - dt V_0
++ dt^2/2 (-M^-1 f_0 - alpha V_0) and keeps f_0 for the first update.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib as L
+from .partition import HaloExchange, Part
+from .solver import Solver
+
+
+class _DeviceArray:
+    """A device buffer of the library exposed through the CUDA array interface."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+def field_view(ctx, which, torch):
+    """(N, 3) float64 or (N, 4) float32 torch view of a library field (one load case)."""
+    ptr, n, lay = L.sbx_field_ptr(ctx, which)
+    if lay == L.SBX_LAYOUT_F32_NODE4:
+        return torch.as_tensor(_DeviceArray(ptr, (n // 4, 4), "<f4"), device="cuda")
+    return torch.as_tensor(_DeviceArray(ptr, (n // 3, 3), "<f8"), device="cuda")
+
+
+class NodeCutSolver:
+    """One part of a node-cut partition on one GPU."""
+
+    def __init__(self, part: Part, mask, h, E, rho, nu, precision="fp64", device=0,
+                 dt=None, alpha=0.0):
+        import torch
+        self.torch = torch
+        self.part = part
+        self.halo = HaloExchange(part)
+        self.stream = torch.cuda.Stream(device=device)
+        c = part.cells
+        self.S = Solver(part.slot_node, np.asarray(mask)[c], np.asarray(h)[c], np.asarray(E)[c],
+                        np.asarray(rho)[c], nu, part.n_nodes, fixed_nodes=part.fixed_nodes,
+                        sources=part.sources, precision=precision, device=device,
+                        stream=self.stream.cuda_stream, dt=dt, alpha=alpha)
+        self.dt_cr_local = self.S.dt_cr
+        self.dt = self.S.dt
+        self.alpha = float(alpha)
+        self.pending = False
+
+    # ---- set-up
+    def pack_mass(self):
+        m = self.S.field(L.SBX_MASS).reshape(-1, 3)
+        return self.halo.pack(self.torch.from_numpy(m))
+
+    def unpack_mass(self, buf):
+        m = self.torch.from_numpy(self.S.field(L.SBX_MASS).reshape(-1, 3).copy())
+        self.halo.unpack(m, buf.cpu())
+        L.sbx_set_mass(self.S.ctx, np.ascontiguousarray(m.numpy().ravel()))
+
+    def set_dt(self, dt):
+        self.dt = float(dt)
+        self.S.dt = self.dt
+
+    def initial_local(self, u0=None, v0=None):
+        """set_initial on the part, then f_0 (local part) into the force buffer."""
+        self.u0, self.v0 = u0, v0
+        self.S.initial(u0, v0)
+        L.sbx_force(self.S.ctx, self.dt)
+        self.pending = True
+
+    def finish_initial(self):
+        """U_-1 from the summed f_0 (Eq. D0 with the interface sum)."""
+        t = self.torch
+        with t.cuda.stream(self.stream):
+            f0 = field_view(self.S.ctx, L.SBX_F_INT, t)[:, :3].double()
+            mass = field_view(self.S.ctx, L.SBX_MASS, t)
+            minv = 1.0 / mass
+            if len(self.part.fixed_nodes):
+                minv[t.as_tensor(self.part.fixed_nodes, device=minv.device)] = 0.0
+            u0 = field_view(self.S.ctx, L.SBX_U_N, t)
+            um1 = field_view(self.S.ctx, L.SBX_U_NM1, t)
+            v0 = (t.as_tensor(np.asarray(self.v0, np.float64).reshape(-1, 3), device=u0.device)
+                  if self.v0 is not None else t.zeros_like(u0))
+            acc = -minv * f0 - self.alpha * v0
+            um1.copy_(u0 - self.dt * v0 + 0.5 * self.dt * self.dt * acc)
+            if len(self.part.fixed_nodes):
+                um1[t.as_tensor(self.part.fixed_nodes, device=um1.device)] = 0.0
+
+    # ---- one step: force -> interface sum -> update
+    def force(self):
+        """Partial force of this part's cells; False when the force buffer
+        already holds the summed force (the start-up's f_0)."""
+        if self.pending:
+            return False
+        L.sbx_force(self.S.ctx, self.dt)
+        self.pending = True
+        return True
+
+    def pack_force(self):
+        t = self.torch
+        with t.cuda.stream(self.stream):
+            buf = self.halo.pack(field_view(self.S.ctx, L.SBX_F_INT, t))
+        t.cuda.current_stream().wait_stream(self.stream)   # the collective runs there
+        return buf
+
+    def unpack_force(self, buf):
+        t = self.torch
+        self.stream.wait_stream(t.cuda.current_stream())
+        with t.cuda.stream(self.stream):
+            self.halo.unpack(field_view(self.S.ctx, L.SBX_F_INT, t), buf)
+
+    def update(self):
+        L.sbx_update(self.S.ctx, self.dt, self.alpha)
+        self.pending = False
+
+    def field(self, which=L.SBX_U_N):
+        self.stream.synchronize()
+        return self.S.field(which)
+
+    def close(self):
+        self.S.close()
+
+
+def step_distributed(engine, n, group=None):
+    """n steps of one rank's engine; the interface sum is an all_reduce."""
+    import torch.distributed as dist
+    for _ in range(n):
+        if engine.force():
+            buf = engine.pack_force()
+            dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+            engine.unpack_force(buf)
+        engine.update()
+
+
+def step_together(engines, n):
+    """n steps of several parts held by one process (summed in place)."""
+    for _ in range(n):
+        fresh = [e.force() for e in engines]
+        if all(fresh):
+            bufs = [e.pack_force() for e in engines]
+            total = bufs[0].clone()
+            for b in bufs[1:]:
+                total += b.to(total.device)
+            for e in engines:
+                e.unpack_force(total)
+        for e in engines:
+            e.update()
+
+
+def setup_together(engines, dt_factor=0.5, u0=None, v0=None):
+    """Mass sum, common dt and start-up for parts held by one process;
+    u0 / v0 are global (N, 3) arrays or None."""
+    total = None
+    for e in engines:
+        b = e.pack_mass()
+        total = b if total is None else total + b
+    for e in engines:
+        e.unpack_mass(total)
+    dt = dt_factor * min(e.dt_cr_local for e in engines)
+    for e in engines:
+        e.set_dt(dt)
+        nodes = e.part.nodes
+        e.initial_local(None if u0 is None else np.ascontiguousarray(np.asarray(u0).reshape(-1, 3)[nodes].ravel()),
+                        None if v0 is None else np.ascontiguousarray(np.asarray(v0).reshape(-1, 3)[nodes].ravel()))
+    bufs = [e.pack_force() for e in engines]
+    tot = bufs[0].clone()
+    for b in bufs[1:]:
+        tot += b
+    for e in engines:
+        e.unpack_force(tot)
+        e.finish_initial()
+    return dt
+
+
+def setup_distributed(engine, dt_factor=0.5, u0=None, v0=None, group=None):
+    """The same set-up for one rank of a torch.distributed job."""
+    import torch
+    import torch.distributed as dist
+    b = engine.pack_mass()
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    b = b.to(dev)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM, group=group)
+    engine.unpack_mass(b)
+    t = torch.tensor([engine.dt_cr_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MIN, group=group)
+    dt = dt_factor * float(t.item())
+    engine.set_dt(dt)
+    nodes = engine.part.nodes
+    engine.initial_local(None if u0 is None else np.ascontiguousarray(np.asarray(u0).reshape(-1, 3)[nodes].ravel()),
+                         None if v0 is None else np.ascontiguousarray(np.asarray(v0).reshape(-1, 3)[nodes].ravel()))
+    buf = engine.pack_force()
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+    engine.unpack_force(buf)
+    engine.finish_initial()
+    return dt

@@ -1,0 +1,152 @@
+"""Node-cut partition of an octree mesh over several GPUs (Sec. 4) and the
+interface sum of the partial internal forces.
+
+Each part holds a contiguous range of cells in the mesh's Morton order (a
+space-filling-curve partition) and every node its cells touch.  Nodes
+touched by more than one part lie on a cut.  Per step every part computes
+the internal force of its own cells (the library's ``sbx_force``), the
+partial forces of the cut nodes are summed over the parts, and every part
+runs the update (``sbx_update``) on all of its nodes; a cut node then has
+the same force, mass and history on every part that holds it, so its
+displacement stays identical everywhere without further exchange.
+
+The sum is one collective per step over a vector that holds every cut node
+once (``HaloExchange``): each part writes its partial forces into the
+positions of its cut nodes, the vectors are summed (``all_reduce`` over
+``torch.distributed`` -- NCCL between GPUs, gloo on CPU), and each part
+reads its positions back.  Point loads on a cut node are applied by the
+lowest part that holds the node, so they are counted once; the lumped mass
+of a cut node is summed the same way once at set-up.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Part:
+    """One part: cells ``cells`` (global ids, ascending), nodes ``nodes``
+    (global ids, ascending; local node id = position), ``slot_node`` in
+    local ids, the cut nodes ``cut_local`` (local ids) and their positions
+    ``cut_pos`` in the global cut vector."""
+    rank: int
+    cells: np.ndarray
+    nodes: np.ndarray
+    slot_node: np.ndarray
+    cut_local: np.ndarray
+    cut_pos: np.ndarray
+    n_cut: int
+    fixed_nodes: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
+    sources: list = field(default_factory=list)
+
+    @property
+    def n_nodes(self):
+        return int(len(self.nodes))
+
+    def local(self, global_nodes):
+        """Local ids of global node ids that this part holds (-1 otherwise)."""
+        g = np.asarray(global_nodes, np.int64)
+        i = np.searchsorted(self.nodes, g)
+        i = np.minimum(i, len(self.nodes) - 1)
+        return np.where(self.nodes[i] == g, i, -1)
+
+
+def split_ranges(n_cells, n_parts, weight=None):
+    """Contiguous cell ranges with near-equal total weight (default: equal
+    counts).  Returns the n_parts + 1 boundaries."""
+    if n_parts < 1 or n_parts > max(1, n_cells):
+        raise ValueError("need 1 <= n_parts <= n_cells")
+    if weight is None:
+        return np.round(np.linspace(0, n_cells, n_parts + 1)).astype(np.int64)
+    c = np.concatenate([[0.0], np.cumsum(np.asarray(weight, np.float64))])
+    targets = c[-1] * np.arange(1, n_parts) / n_parts
+    inner = np.searchsorted(c, targets)
+    b = np.concatenate([[0], inner, [n_cells]]).astype(np.int64)
+    for k in range(1, n_parts + 1):   # keep every part non-empty
+        b[k] = max(b[k], b[k - 1] + 1)
+    for k in range(n_parts - 1, -1, -1):
+        b[k] = min(b[k], b[k + 1] - 1)
+    return b
+
+
+def partition(slot_node, n_parts, fixed_nodes=(), sources=(), weight=None):
+    """Split the cells (rows of ``slot_node``, in Morton order) into
+    ``n_parts`` contiguous ranges and build each part's local numbering and
+    cut lists.  ``weight`` (per cell, optional) balances the ranges, e.g. by
+    the contraction cost m_p^2."""
+    slot_node = np.asarray(slot_node)
+    C = slot_node.shape[0]
+    b = split_ranges(C, n_parts, weight)
+    node_sets = []
+    for k in range(n_parts):
+        sn = slot_node[b[k]:b[k + 1]]
+        node_sets.append(np.unique(sn[sn >= 0]))
+    # cut nodes: held by >= 2 parts
+    allnodes = np.concatenate(node_sets)
+    uniq, counts = np.unique(allnodes, return_counts=True)
+    cut = uniq[counts >= 2]
+    # lowest part holding each node (point loads go there)
+    owner = {}
+    for k in range(n_parts - 1, -1, -1):
+        for q in node_sets[k]:
+            owner[int(q)] = k
+    fixed_nodes = np.asarray(fixed_nodes, np.int64)
+    parts = []
+    for k in range(n_parts):
+        nodes = node_sets[k]
+        sn = slot_node[b[k]:b[k + 1]]
+        loc = np.full(sn.shape, -1, np.int64)
+        m = sn >= 0
+        loc[m] = np.searchsorted(nodes, sn[m])
+        in_cut = np.isin(nodes, cut)
+        cut_local = np.nonzero(in_cut)[0].astype(np.int64)
+        cut_pos = np.searchsorted(cut, nodes[cut_local]).astype(np.int64)
+        P = Part(rank=k, cells=np.arange(b[k], b[k + 1], dtype=np.int64), nodes=nodes,
+                 slot_node=loc.astype(slot_node.dtype), cut_local=cut_local, cut_pos=cut_pos,
+                 n_cut=int(len(cut)))
+        fl = P.local(fixed_nodes) if len(fixed_nodes) else np.zeros(0, np.int64)
+        P.fixed_nodes = fl[fl >= 0]
+        for s in sources:
+            if owner.get(int(s["node"])) == k:
+                t = dict(s)
+                t["node"] = int(P.local([s["node"]])[0])
+                P.sources.append(t)
+        parts.append(P)
+    return parts
+
+
+class HaloExchange:
+    """Sum of the cut nodes' values over the parts.
+
+    ``pack(v)`` copies this part's cut-node rows of ``v`` (a (N_local, k)
+    tensor or array) into a zeroed global cut vector (n_cut, k);
+    ``unpack(v, buf)`` writes the summed rows back.  ``exchange(v)`` does
+    both around one ``all_reduce`` (``torch.distributed``, default group)."""
+
+    def __init__(self, part: Part):
+        self.part = part
+
+    def pack(self, v):
+        import torch
+        t = v if isinstance(v, torch.Tensor) else torch.from_numpy(np.asarray(v))
+        idx = torch.as_tensor(self.part.cut_local, device=t.device)
+        pos = torch.as_tensor(self.part.cut_pos, device=t.device)
+        buf = torch.zeros((self.part.n_cut,) + tuple(t.shape[1:]), dtype=t.dtype, device=t.device)
+        buf.index_copy_(0, pos, t.index_select(0, idx))
+        return buf
+
+    def unpack(self, v, buf):
+        import torch
+        t = v if isinstance(v, torch.Tensor) else torch.from_numpy(v)
+        idx = torch.as_tensor(self.part.cut_local, device=t.device)
+        pos = torch.as_tensor(self.part.cut_pos, device=t.device)
+        t.index_copy_(0, idx, buf.index_select(0, pos))
+
+    def exchange(self, v, group=None):
+        import torch.distributed as dist
+        buf = self.pack(v)
+        dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+        self.unpack(v, buf)
+        return v

@@ -1,0 +1,214 @@
+"""Node-cut partition and interface sum (host logic, CPU).
+
+The product's partition, HaloExchange and the torch.distributed step
+driver run here with the FP64 oracle as each part's local force engine
+(the GPU engine is tested in test_gpu_nodecut.py): the parts' stepped
+states must equal the single-domain oracle run at every node."""
+import copy
+import os
+import socket
+import tempfile
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import octree_gen as og
+from oracle import assembly, cdm
+from paper_2103_09100_gb300 import nodecut
+from paper_2103_09100_gb300.partition import HaloExchange, partition, split_ranges
+
+
+def sub_mesh(mesh, part):
+    m = copy.copy(mesh)
+    c = part.cells
+    m.level, m.anchor, m.h, m.mask = mesh.level[c], mesh.anchor[c], mesh.h[c], mesh.mask[c]
+    m.E, m.rho = mesh.E[c], mesh.rho[c]
+    m.slot_node = part.slot_node
+    m.node_xyz = mesh.node_xyz[part.nodes]
+    m.fixed_nodes = part.fixed_nodes
+    m.sources = part.sources
+    return m
+
+
+class OracleEngine:
+    """One part stepped by the FP64 oracle (test double of the GPU engine)."""
+
+    def __init__(self, mesh, part, alpha=0.0):
+        self.part, self.halo, self.alpha = part, HaloExchange(part), alpha
+        self.sub = sub_mesh(mesh, part)
+        self.P = cdm.make_problem(self.sub)
+        self.dt_cr_local = assembly.critical_dt(self.sub)
+        self.M = self.P.M_diag.copy()
+        self.pending = False
+
+    def pack_mass(self):
+        return self.halo.pack(torch.from_numpy(self.M.reshape(-1, 3).copy()))
+
+    def unpack_mass(self, buf):
+        m = torch.from_numpy(self.M.reshape(-1, 3).copy())
+        self.halo.unpack(m, buf)
+        self.M = m.numpy().ravel().copy()
+
+    def set_dt(self, dt):
+        self.dt = dt
+        self.P = cdm.make_problem(self.sub, dt=dt, alpha=self.alpha)
+
+    def initial_local(self, u0=None, v0=None):
+        n = self.P.n_dof
+        self.u = np.zeros(n) if u0 is None else np.array(u0, float)
+        self.v0 = np.zeros(n) if v0 is None else np.array(v0, float)
+        self.u[self.P.fixed] = 0.0
+        self.v0[self.P.fixed] = 0.0
+        self.n = 0
+        self.f = cdm.apply_K(self.P, self.u) - cdm.external_force(self.P, 0)
+        self.pending = True
+
+    def pack_force(self):
+        return self.halo.pack(torch.from_numpy(self.f.reshape(-1, 3)))
+
+    def unpack_force(self, buf):
+        self.halo.unpack(torch.from_numpy(self.f.reshape(-1, 3)), buf)
+
+    def finish_initial(self):
+        minv = 1.0 / self.M
+        minv[self.P.fixed] = 0.0
+        acc = -minv * self.f - self.alpha * self.v0
+        self.up = self.u - self.dt * self.v0 + 0.5 * self.dt ** 2 * acc
+        self.up[self.P.fixed] = 0.0
+
+    def force(self):
+        if self.pending:
+            return False
+        self.f = cdm.apply_K(self.P, self.u) - cdm.external_force(self.P, self.n)
+        self.pending = True
+        return True
+
+    def update(self):
+        w = self.dt ** 2 / self.M / (1 + 0.5 * self.alpha * self.dt)
+        w[self.P.fixed] = 0.0
+        a, b = 2.0 / (1 + 0.5 * self.alpha * self.dt), (1 - 0.5 * self.alpha * self.dt) / (1 + 0.5 * self.alpha * self.dt)
+        un = a * self.u - b * self.up - w * self.f
+        self.up, self.u = self.u, un
+        self.n += 1
+        self.pending = False
+
+
+def _mesh():
+    m = og.config_corner_cube()
+    m.E = np.exp(0.3 * np.random.default_rng(7).standard_normal(m.n_cells))
+    return m
+
+
+def test_split_ranges():
+    b = split_ranges(10, 3)
+    assert b[0] == 0 and b[-1] == 10 and np.all(np.diff(b) > 0)
+    w = np.ones(100); w[:10] = 10.0
+    b = split_ranges(100, 2, w)
+    assert abs(w[:b[1]].sum() - w[b[1]:].sum()) <= 10.0
+    with pytest.raises(ValueError):
+        split_ranges(3, 4)
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 5])
+def test_partition_invariants(P):
+    m = _mesh()
+    parts = partition(m.slot_node, P, fixed_nodes=m.fixed_nodes, sources=m.sources)
+    cells = np.concatenate([p.cells for p in parts])
+    assert np.array_equal(cells, np.arange(m.n_cells))
+    held = np.zeros(m.n_nodes, int)
+    for p in parts:
+        sn = m.slot_node[p.cells]
+        assert np.array_equal(p.nodes, np.unique(sn[sn >= 0]))
+        back = np.where(p.slot_node >= 0, p.nodes[np.maximum(p.slot_node, 0)], -1)
+        assert np.array_equal(back, sn)
+        held[p.nodes] += 1
+        assert np.array_equal(np.sort(p.nodes[p.cut_local]), p.nodes[p.cut_local])
+    cut = np.nonzero(held >= 2)[0]
+    assert held.min() >= 1
+    for p in parts:
+        assert p.n_cut == len(cut)
+        assert np.array_equal(cut[p.cut_pos], p.nodes[p.cut_local])
+        assert np.array_equal(np.isin(p.nodes, cut), np.isin(np.arange(p.n_nodes), p.cut_local))
+    # every source in exactly one part; every fixed node wherever it is held
+    assert sum(len(p.sources) for p in parts) == len(m.sources)
+    for p in parts:
+        assert set(p.nodes[p.fixed_nodes]) == set(m.fixed_nodes) & set(p.nodes)
+
+
+@pytest.mark.parametrize("P", [2, 4])
+def test_interface_sum_gives_global_force(P):
+    m = _mesh()
+    Pg = cdm.make_problem(m)
+    u = np.random.default_rng(1).standard_normal(m.n_dof)
+    fg = cdm.apply_K(Pg, u).reshape(-1, 3)
+    parts = partition(m.slot_node, P)
+    halos = [HaloExchange(p) for p in parts]
+    fl = []
+    for p in parts:
+        Pl = cdm.make_problem(sub_mesh(m, p))
+        fl.append(torch.from_numpy(cdm.apply_K(Pl, u.reshape(-1, 3)[p.nodes].ravel()).reshape(-1, 3)))
+    total = sum(h.pack(f) for h, f in zip(halos, fl))
+    for h, f, p in zip(halos, fl, parts):
+        h.unpack(f, total)
+        assert np.abs(f.numpy() - fg[p.nodes]).max() <= 1e-12 * np.abs(fg).max()
+
+
+def test_steps_together_equal_global_oracle():
+    m = _mesh()
+    parts = partition(m.slot_node, 3, fixed_nodes=m.fixed_nodes, sources=m.sources)
+    eng = [OracleEngine(m, p) for p in parts]
+    rng = np.random.default_rng(2)
+    u0 = rng.standard_normal(m.n_dof) * 1e-3
+    v0 = rng.standard_normal(m.n_dof) * 1e-3
+    dt = nodecut.setup_together(eng, 0.5, u0=u0, v0=v0)
+    nodecut.step_together(eng, 40)
+    Pg = cdm.make_problem(m, dt=dt)
+    u, up = cdm.initial_state(Pg, u0, v0)
+    u, _, _, _ = cdm.run(Pg, 40, u, up)
+    ug = u.reshape(-1, 3)
+    for e in eng:
+        assert np.abs(e.u.reshape(-1, 3) - ug[e.part.nodes]).max() <= 1e-12 * np.abs(ug).max()
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, out_dir, n_steps):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank,
+                            world_size=world)
+    try:
+        m = _mesh()
+        parts = partition(m.slot_node, world, fixed_nodes=m.fixed_nodes, sources=m.sources)
+        e = OracleEngine(m, parts[rank])
+        u0 = np.random.default_rng(2).standard_normal(m.n_dof) * 1e-3
+        dt = nodecut.setup_distributed(e, 0.5, u0=u0)
+        nodecut.step_distributed(e, n_steps)
+        np.savez(os.path.join(out_dir, "r%d.npz" % rank), u=e.u, nodes=e.part.nodes, dt=dt)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_two_ranks_equal_global_oracle():
+    mp = pytest.importorskip("torch.multiprocessing")
+    n_steps = 30
+    with tempfile.TemporaryDirectory() as d:
+        mp.spawn(_rank_main, args=(2, _free_port(), d, n_steps), nprocs=2, join=True)
+        res = [np.load(os.path.join(d, "r%d.npz" % r)) for r in range(2)]
+    m = _mesh()
+    dt = float(res[0]["dt"])
+    assert dt == float(res[1]["dt"])
+    Pg = cdm.make_problem(m, dt=dt)
+    u0 = np.random.default_rng(2).standard_normal(m.n_dof) * 1e-3
+    u, up = cdm.initial_state(Pg, u0)
+    u, _, _, _ = cdm.run(Pg, n_steps, u, up)
+    ug = u.reshape(-1, 3)
+    for r in res:
+        assert np.abs(r["u"].reshape(-1, 3) - ug[r["nodes"]]).max() <= 1e-12 * np.abs(ug).max()
