@@ -55,8 +55,11 @@ typedef struct sbx_ctx sbx_ctx;
 
 /* precision modes of mesh_upload (the displacement history is FP64 in all) */
 #define SBX_PREC_FP64   0  /* K_p u_e in FP64 (DFMA)                           */
-#define SBX_PREC_MIXED  1  /* K_p u_e as three TF32 tensor-core products of
-                              split operands, FP32 accumulation (tcgen05)     */
+#define SBX_PREC_MIXED  1  /* 8-node cells: K_p u_e as three TF32 tensor-core
+                              products of split operands, FP32 accumulation
+                              (tcgen05); other patterns: FP32 FFMA.  Both on
+                              each cell's displacements relative to its
+                              slot-0 node                                     */
 #define SBX_PREC_FP32   2  /* K_p u_e in FP32 (FFMA), FP64 scale and update   */
 
 /* fields of read_field / write_field */
@@ -290,11 +293,14 @@ int sbx_set_mass(sbx_ctx *ctx, const double *mass);
  *   what = SBX_Q_KERNELS_PER_STEP  kernel launches per step (force + update)
  *          SBX_Q_FORCE_LAUNCHES    force-kernel launches per step
  *          SBX_Q_TILES             CTAs of all force launches of one step
+ *          SBX_Q_BRICK_TILES       mixed form: tensor-core tiles that are
+ *                                  complete 4 x 4 x 8 blocks of 8-node cells
  *   Errors: SBX_ESTATE (no mesh), SBX_EINVAL (unknown item, NULL out).
  */
 #define SBX_Q_KERNELS_PER_STEP 0
 #define SBX_Q_FORCE_LAUNCHES   1
 #define SBX_Q_TILES            2
+#define SBX_Q_BRICK_TILES      3
 int sbx_query(sbx_ctx *ctx, int what, int64_t *out);
 
 /*

@@ -35,7 +35,15 @@
 // group (LBO = 128 B, SBO = nK * 128 B).  TMEM columns: D 0..31, A_hi
 // 32..55, A_lo 64..87.
 //
-// Tile record of k_force_tc (every part padded to 16 bytes):
+// Tile records of k_force_tc (every part padded to 16 bytes), two kinds:
+//  brick (kind 1): 128 same-size cells forming a complete 4 x 4 x 8 block,
+//   cell c at (c & 3, (c >> 2) & 3, c >> 4), nodes on the 5 x 5 x 9 lattice,
+//   node (a, b, c) = index a + 5 b + 25 c; slot k = corner (k & 1, k >> 1 & 1,
+//   k >> 2); every index is arithmetic.
+//   int32 {pat, 128, 225, 1}           header
+//   float scale[128]                   E_e h_e rounded to FP32
+//   int32 nodes[225]                   lattice node ids
+//  list (kind 0): any cells (up to 128):
 //   int32 {pat, ncell, nn, 0}          header
 //   float scale[ncell]                 E_e h_e rounded to FP32
 //   int32 nodes[nn]                    unique node ids, ascending
@@ -68,17 +76,24 @@ constexpr int GEN_TILE = 32;       // cells per k_force_gen CTA
 __host__ __device__ inline uint32_t a16(uint32_t x) { return (x + 15u) & ~15u; }
 __host__ __device__ inline uint32_t a128(uint32_t x) { return (x + 127u) & ~127u; }
 
+constexpr int BRICK_NX = 4, BRICK_NY = 4, BRICK_NZ = 8;   // cells of a brick tile
+constexpr int BRICK_CELLS = BRICK_NX * BRICK_NY * BRICK_NZ;  // 128
+constexpr int BRICK_NODES = 5 * 5 * 9;                      // 225
+
 struct RecLayout {
   uint32_t scale, nodes, lid, off, inc, bytes;
 };
-__host__ __device__ inline RecLayout rec_layout(int ncell, int nn) {
+__host__ __device__ inline RecLayout rec_layout(int ncell, int nn, int kind) {
   RecLayout R;
   uint32_t o = 16;
   R.scale = o; o += a16(4u * ncell);
   R.nodes = o; o += a16(4u * nn);
-  R.lid = o;   o += a16(16u * ncell);
-  R.off = o;   o += a16(2u * (nn + 1));
-  R.inc = o;   o += a16(16u * ncell);
+  R.lid = R.off = R.inc = o;
+  if (kind == 0) {
+    R.lid = o; o += a16(16u * ncell);
+    R.off = o; o += a16(2u * (nn + 1));
+    R.inc = o; o += a16(16u * ncell);
+  }
   R.bytes = o;
   return R;
 }
@@ -111,7 +126,7 @@ struct Stage {
 __device__ inline Stage stage_view(const unsigned char *base, uint32_t u_off) {
   Stage S;
   S.hdr = reinterpret_cast<const int32_t *>(base);
-  const RecLayout R = rec_layout(S.hdr[1], S.hdr[2]);
+  const RecLayout R = rec_layout(S.hdr[1], S.hdr[2], S.hdr[3]);
   S.scale = reinterpret_cast<const float *>(base + R.scale);
   S.nodes = reinterpret_cast<const int32_t *>(base + R.nodes);
   S.lid = reinterpret_cast<const uint16_t *>(base + R.lid);
@@ -248,6 +263,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
     }
     const Stage S = stage_view(stage_base(s), SL.u_off);
     const int ncell = S.hdr[1], nn = S.hdr[2];
+    const bool brick = S.hdr[3] == 1;
     // A rows: differences to slot 0, TF32 hi + lo, into TMEM columns
     // COL_AHI / COL_ALO + 12 h .. + 11 of lane = cell (rows past ncell: 0)
     {
@@ -255,9 +271,19 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
 #pragma unroll
       for (int q = 0; q < 12; ++q) vh[q] = vl[q] = 0.0f;
       if (fc < ncell) {
-        const uint4 L = *reinterpret_cast<const uint4 *>(S.lid + 8 * fc);
-        const uint32_t lw0 = fh ? L.z : L.x, lw1 = fh ? L.w : L.y;
-        const float *ref = S.u + 6 * (L.x & 0xFFFFu);
+        uint32_t lw0, lw1, l0;   // local node indices of slots 4h .. 4h + 3 (2 x u16), slot 0
+        if (brick) {   // lattice: slot k = corner (k & 1, k >> 1 & 1, k >> 2)
+          const int b0 = (fc & 3) + 5 * ((fc >> 2) & 3) + 25 * (fc >> 4) + 25 * fh;
+          l0 = (uint32_t)(b0 - 25 * fh);
+          lw0 = (uint32_t)b0 | (uint32_t)(b0 + 1) << 16;
+          lw1 = (uint32_t)(b0 + 5) | (uint32_t)(b0 + 6) << 16;
+        } else {
+          const uint4 L = *reinterpret_cast<const uint4 *>(S.lid + 8 * fc);
+          lw0 = fh ? L.z : L.x;
+          lw1 = fh ? L.w : L.y;
+          l0 = L.x & 0xFFFFu;
+        }
+        const float *ref = S.u + 6 * l0;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const uint32_t lk = ((t < 2 ? lw0 : lw1) >> (16 * (t & 1))) & 0xFFFFu;
@@ -329,7 +355,23 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
     }
     __syncthreads();
     // node sums over the incidences (cell, slot): at most 8 per node
-    {
+    if (brick) {   // node (a, b, c) gets corner (dx, dy, dz) of cell (a - dx, b - dy, c - dz)
+      for (int q = tid; q < BRICK_NODES; q += TC_THREADS) {
+        const int a = q % 5, b = (q / 5) % 5, c = q / 25;
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int x = a - (k & 1), y = b - ((k >> 1) & 1), z = c - (k >> 2);
+          if (x >= 0 && x < BRICK_NX && y >= 0 && y < BRICK_NY && z >= 0 && z < BRICK_NZ) {
+            const float4 w = F4[k * 128 + x + BRICK_NX * y + BRICK_NX * BRICK_NY * z];
+            a0 += w.x;
+            a1 += w.y;
+            a2 += w.z;
+          }
+        }
+        red_add_v4(f4 + 4 * (int64_t)S.nodes[q], a0, a1, a2);
+      }
+    } else {
       for (int q = tid; q < nn; q += TC_THREADS) {
         float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
         const int j0 = S.off[q], nj = S.off[q + 1] - j0;
@@ -503,6 +545,7 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   std::vector<int64_t> kpoff(P, 0);
   std::vector<int64_t> mark(ctx->N, -1);   // node -> last tile that holds it
   int64_t stamp = 0;
+  ctx->n_brick_tiles = 0;
   for (int p = 0; p < P; ++p) {
     if (cnt[p] == 0) continue;
     const int np = ctx->pat_nodes[p], m = 3 * np;
@@ -535,19 +578,87 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
         Bhl[o] = hi;
         Bhl[(size_t)NPAD * KPAD + o] = lo;
       }
+    const int64_t Cp = cnt[p];
+    auto corner = [&](int64_t j, int k) { return conn[conn_off[p] + (int64_t)k * Cp + j]; };
+    // bricks: complete 4 x 4 x 8 blocks of same-size cells, found from the
+    // connectivity (the +x / +y / +z neighbour of a cell is the cell whose
+    // slot-0 node is its slot 1 / 2 / 4 node), greedily in Morton order
+    std::vector<int64_t> c0(ctx->N, -1);
+    for (int64_t j = 0; j < Cp; ++j) c0[corner(j, 0)] = j;
+    auto step = [&](int64_t j, int k) -> int64_t {
+      if (j < 0) return -1;
+      const int64_t n = c0[corner(j, k)];
+      return (n >= 0 && ctx->h_hs[start[p] + n] == ctx->h_hs[start[p] + j]) ? n : -1;
+    };
+    std::vector<char> used(Cp, 0);
+    std::vector<std::pair<int64_t, TcTile>> ptiles;   // (first cell, tile) for ordering
+    std::vector<int64_t> bc(BRICK_CELLS);
+    for (int64_t j = 0; j < Cp; ++j) {
+      if (used[j]) continue;
+      bool ok = true;
+      int64_t zc = j;
+      for (int z = 0; z < BRICK_NZ && ok; ++z) {
+        int64_t yc = zc;
+        for (int y = 0; y < BRICK_NY && ok; ++y) {
+          int64_t xc = yc;
+          for (int x = 0; x < BRICK_NX && ok; ++x) {
+            if (xc < 0 || used[xc]) {
+              ok = false;
+              break;
+            }
+            bc[x + BRICK_NX * y + BRICK_NX * BRICK_NY * z] = xc;
+            if (x + 1 < BRICK_NX) xc = step(xc, 1);
+          }
+          if (y + 1 < BRICK_NY) yc = step(yc, 2);
+        }
+        if (z + 1 < BRICK_NZ) zc = step(zc, 4);
+      }
+      if (!ok) continue;
+      int32_t nodes[BRICK_NODES];
+      for (int q = 0; q < BRICK_NODES; ++q) {
+        const int a = q % 5, b = (q / 5) % 5, c = q / 25;
+        const int x = std::min(a, 3), y = std::min(b, 3), z = std::min(c, 7);
+        nodes[q] = corner(bc[x + 4 * y + 16 * z], (a - x) + 2 * (b - y) + 4 * (c - z));
+      }
+      float sc[BRICK_CELLS];
+      for (int c = 0; c < BRICK_CELLS; ++c) {
+        used[bc[c]] = 1;
+        sc[c] = (float)scale_sorted[start[p] + bc[c]];
+      }
+      const RecLayout R = rec_layout(BRICK_CELLS, BRICK_NODES, 1);
+      const size_t at = recs.size();
+      recs.resize(at + R.bytes, 0);
+      const int32_t hdr[4] = {p, BRICK_CELLS, BRICK_NODES, 1};
+      put(recs, at, hdr, 4);
+      put(recs, at + R.scale, sc, BRICK_CELLS);
+      put(recs, at + R.nodes, nodes, BRICK_NODES);
+      TcTile t;
+      t.rec_off = (int64_t)at;
+      t.rec_bytes = (int32_t)R.bytes;
+      t.pat = p;
+      recmax = std::max(recmax, (int)R.bytes);
+      nnmax = std::max(nnmax, BRICK_NODES);
+      ptiles.emplace_back(j, t);
+      ++ctx->n_brick_tiles;
+    }
+    // the other cells: list tiles, greedy cut at 128 cells or
+    // FAST_NN_CAP unique nodes
+    std::vector<int64_t> rest;
+    for (int64_t j = 0; j < Cp; ++j)
+      if (!used[j]) rest.push_back(j);
     std::vector<std::pair<int32_t, int32_t>> v;   // (node, cell * 32 + slot)
-    for (int64_t c0 = 0, nc = 0; c0 < cnt[p]; c0 += nc) {
-      // greedy cut: up to 128 cells, at most FAST_NN_CAP unique nodes
+    for (size_t r0 = 0, nc = 0; r0 < rest.size(); r0 += nc) {
       ++stamp;
       int nn_new = 0;
       nc = 0;
-      while (c0 + nc < cnt[p] && nc < 128) {
+      while (r0 + nc < rest.size() && nc < 128) {
+        const int64_t j = rest[r0 + nc];
         int add = 0;
         for (int k = 0; k < 8; ++k)
-          if (mark[conn[conn_off[p] + (int64_t)k * cnt[p] + c0 + nc]] != stamp) ++add;
+          if (mark[corner(j, k)] != stamp) ++add;
         if (nc > 0 && nn_new + add > FAST_NN_CAP) break;
         for (int k = 0; k < 8; ++k) {
-          const int32_t q = conn[conn_off[p] + (int64_t)k * cnt[p] + c0 + nc];
+          const int32_t q = corner(j, k);
           if (mark[q] != stamp) {
             mark[q] = stamp;
             ++nn_new;
@@ -557,8 +668,7 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
       }
       v.clear();
       for (int k = 0; k < 8; ++k)
-        for (int c = 0; c < nc; ++c)
-          v.emplace_back(conn[conn_off[p] + (int64_t)k * cnt[p] + c0 + c], c * 32 + k);
+        for (size_t c = 0; c < nc; ++c) v.emplace_back(corner(rest[r0 + c], k), (int32_t)(c * 32 + k));
       std::sort(v.begin(), v.end());
       std::vector<int32_t> nodes;
       std::vector<uint16_t> lid((size_t)8 * nc, 0), offs, inc;
@@ -572,11 +682,11 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
       }
       offs.push_back((uint16_t)inc.size());
       const int nn = (int)nodes.size();
-      const RecLayout R = rec_layout((int)nc, nn);
+      const RecLayout R = rec_layout((int)nc, nn, 0);
       const size_t at = recs.size();
       recs.resize(at + R.bytes, 0);
       std::vector<float> sc(nc);
-      for (int c = 0; c < nc; ++c) sc[c] = (float)scale_sorted[start[p] + c0 + c];
+      for (size_t c = 0; c < nc; ++c) sc[c] = (float)scale_sorted[start[p] + rest[r0 + c]];
       const int32_t hdr[4] = {p, (int32_t)nc, nn, 0};
       put(recs, at, hdr, 4);
       put(recs, at + R.scale, sc.data(), nc);
@@ -590,8 +700,15 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
       t.pat = p;
       recmax = std::max(recmax, (int)R.bytes);
       nnmax = std::max(nnmax, nn);
-      tiles.push_back(t);
+      ptiles.emplace_back(rest[r0], t);
     }
+    // tiles in Morton order of their first cell (neighbouring tiles run
+    // together and share nodes in L2)
+    std::stable_sort(ptiles.begin(), ptiles.end(),
+                     [](const std::pair<int64_t, TcTile> &a, const std::pair<int64_t, TcTile> &b) {
+                       return a.first < b.first;
+                     });
+    for (auto &pt : ptiles) tiles.push_back(pt.second);
   }
   auto up = [&](auto **dst, const auto &vec) -> int {
     using T = typename std::remove_reference<decltype(vec)>::type::value_type;

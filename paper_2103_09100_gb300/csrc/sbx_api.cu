@@ -479,6 +479,9 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   ctx->prec = precision_mode;
   ctx->B = n_rhs;
   ctx->N = n_nodes;
+  ctx->h_order = order;
+  ctx->h_hs.resize(n_cells);
+  for (int64_t s = 0; s < n_cells; ++s) ctx->h_hs[s] = hv[order[s]];
   if (n_rhs > 1) {
     std::string e;
     const int brc = sbx::batch_setup(ctx, conn, conn_off, cnt, ssym, scale, start, e);
@@ -508,9 +511,6 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   ctx->B = n_rhs;
   ctx->prec = precision_mode;
   ctx->pat_cstart = start;
-  ctx->h_order = order;
-  ctx->h_hs.resize(n_cells);
-  for (int64_t s = 0; s < n_cells; ++s) ctx->h_hs[s] = hv[order[s]];
   ctx->pat_ccount = cnt;
   ctx->n_tiles_simt = (int)tiles.size();
   ctx->max_m = max_m;
@@ -948,6 +948,7 @@ int sbx_query(sbx_ctx *ctx, int what, int64_t *out) {
     case SBX_Q_KERNELS_PER_STEP: *out = launches + 1; break;
     case SBX_Q_FORCE_LAUNCHES: *out = launches; break;
     case SBX_Q_TILES: *out = tiles; break;
+    case SBX_Q_BRICK_TILES: *out = (ctx->prec == SBX_PREC_MIXED && ctx->B == 1) ? ctx->n_brick_tiles : 0; break;
     default: return fail(ctx, SBX_EINVAL, "unknown query");
   }
   return SBX_OK;

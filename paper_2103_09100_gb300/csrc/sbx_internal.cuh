@@ -126,6 +126,7 @@ struct sbx_ctx {
   int tc_rec_max[sbx::TC_CLASSES] = {}, tc_nn_max[sbx::TC_CLASSES] = {};
   int tc_grid[sbx::TC_CLASSES] = {};
   size_t tc_smem[sbx::TC_CLASSES] = {};
+  int n_brick_tiles = 0;           // of n_tc_tiles[0]: complete 4 x 4 x 8 blocks
   sbx::Tile *d_gen_tiles = nullptr;
   float *d_gen_K = nullptr;        // FP32 K_p of those patterns, rows padded to a multiple of 4
   int64_t *d_gen_koff = nullptr;

@@ -89,3 +89,33 @@ def test_mixed_receiver_cube_force_and_100_steps():
     e = rel(S.field(L.SBX_U_N), u)
     print("receiver cube mixed 100-step rel error %.3e" % e)
     assert e < 1e-5
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_mixed_uniform_bricks(n):
+    # n^3 uniform cells: every cell in a complete 4 x 4 x 8 brick tile
+    m = og.small_uniform(n)
+    m.E = np.exp(0.3 * np.random.default_rng(n).standard_normal(m.n_cells))
+    m.fixed_nodes = np.where(np.abs(m.node_xyz[:, 2]) < 1e-12)[0]
+    P = cdm.make_problem(m)
+    S = Solver.from_mesh(m, precision="mixed", dt=P.dt)
+    assert L.sbx_query(S.ctx, L.SBX_Q_BRICK_TILES) == n ** 3 // 128
+    u0 = np.random.default_rng(n + 1).standard_normal(m.n_dof)
+    u0[P.fixed] = 0
+    S.initial(u0)
+    S.step(1)
+    ref = cdm.apply_K(P, u0) - cdm.external_force(P, 0)
+    assert rel(S.field(L.SBX_F_INT), ref) < 1e-5
+    u, up = cdm.initial_state(P, u0)
+    S.initial(u0)
+    S.step(100)
+    u, up, _, _ = cdm.run(P, 100, u, up, threads=16)
+    assert rel(S.field(L.SBX_U_N), u) < 1e-5
+
+
+def test_mixed_brick_and_list_tiles_cavity_counts():
+    m = og.config_receiver_cube()
+    S = Solver.from_mesh(m, precision="mixed")
+    nb = L.sbx_query(S.ctx, L.SBX_Q_BRICK_TILES)
+    print("receiver cube: %d brick tiles of %d tensor-core + SIMT tiles" % (nb, L.sbx_query(S.ctx, L.SBX_Q_TILES)))
+    assert nb > 0
