@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
     if (!ok) break;
     ph_mma ^= 1u;
     // epilogue: warps w and w + 4 read TMEM lanes 32 (w % 4) .. + 31, columns
-    // 12 h .. 12 h + 11; F4[slot][cell] = E h D
+    // 12 h .. 12 h + 11 (cell, slots 4 h .. 4 h + 3) times E h
     {
       float v[12];
       {
@@ -344,34 +344,55 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
 #pragma unroll
         for (int q = 0; q < 4; ++q) v[8 + q] = __uint_as_float(r4[q]);
       }
-      if (fc < ncell) {
+      tc::fence_before_sync();
+      if (brick) {
+        // lane = x + 4 y + 16 zl holds corners (dx, dy, dz = h) of cell
+        // (x, y, z = 2 (w % 4) + zl); the node (a, b) of lattice layer z + h
+        // sums corner (dx, dy) of the cells (a - dx, b - dy): lane (x, y) forms
+        // node (x, y) (and (4, y), (x, 4), (4, 4) on the +x / +y rows) from
+        // its own corners and its -x, -y, -x-y neighbours' (warp shuffles)
+        const int lane = tid & 31, x = lane & 3, y = (lane >> 2) & 3;
+        const float sc = S.scale[fc];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) v[q] *= sc;
+        float s1[6], s4[6], s5[3];   // from lane - 1: corners 1, 3; lane - 4: 2, 3; lane - 5: 3
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          s1[r] = __shfl_up_sync(0xffffffffu, v[3 + r], 1);
+          s1[3 + r] = __shfl_up_sync(0xffffffffu, v[9 + r], 1);
+          s4[r] = __shfl_up_sync(0xffffffffu, v[6 + r], 4);
+          s4[3 + r] = __shfl_up_sync(0xffffffffu, v[9 + r], 4);
+          s5[r] = __shfl_up_sync(0xffffffffu, v[9 + r], 5);
+        }
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {   // neighbours outside the layer contribute nothing
+          s1[r] = x > 0 ? s1[r] : 0.0f;
+          s4[r] = y > 0 ? s4[r] : 0.0f;
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) s5[r] = (x > 0 && y > 0) ? s5[r] : 0.0f;
+        const int base = 25 * (2 * (warp & 3) + ((lane >> 4) & 1) + fh);
+        red_add_v4(f4 + 4 * (int64_t)S.nodes[base + x + 5 * y], v[0] + s1[0] + s4[0] + s5[0],
+                   v[1] + s1[1] + s4[1] + s5[1], v[2] + s1[2] + s4[2] + s5[2]);
+        if (x == 3)   // node (4, y): own corner (1, 0), cell (3, y - 1) corner (1, 1)
+          red_add_v4(f4 + 4 * (int64_t)S.nodes[base + 4 + 5 * y], v[3] + s4[3], v[4] + s4[4],
+                     v[5] + s4[5]);
+        if (y == 3)   // node (x, 4): own corner (0, 1), cell (x - 1, 3) corner (1, 1)
+          red_add_v4(f4 + 4 * (int64_t)S.nodes[base + x + 20], v[6] + s1[3], v[7] + s1[4],
+                     v[8] + s1[5]);
+        if (x == 3 && y == 3)   // node (4, 4)
+          red_add_v4(f4 + 4 * (int64_t)S.nodes[base + 24], v[9], v[10], v[11]);
+      } else if (fc < ncell) {
         const float sc = S.scale[fc];
 #pragma unroll
         for (int t = 0; t < 4; ++t)
           F4[(4 * fh + t) * 128 + fc] =
               make_float4(sc * v[3 * t], sc * v[3 * t + 1], sc * v[3 * t + 2], 0.0f);
       }
-      tc::fence_before_sync();
     }
     __syncthreads();
-    // node sums over the incidences (cell, slot): at most 8 per node
-    if (brick) {   // node (a, b, c) gets corner (dx, dy, dz) of cell (a - dx, b - dy, c - dz)
-      for (int q = tid; q < BRICK_NODES; q += TC_THREADS) {
-        const int a = q % 5, b = (q / 5) % 5, c = q / 25;
-        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int x = a - (k & 1), y = b - ((k >> 1) & 1), z = c - (k >> 2);
-          if (x >= 0 && x < BRICK_NX && y >= 0 && y < BRICK_NY && z >= 0 && z < BRICK_NZ) {
-            const float4 w = F4[k * 128 + x + BRICK_NX * y + BRICK_NX * BRICK_NY * z];
-            a0 += w.x;
-            a1 += w.y;
-            a2 += w.z;
-          }
-        }
-        red_add_v4(f4 + 4 * (int64_t)S.nodes[q], a0, a1, a2);
-      }
-    } else {
+    // list tiles: node sums over the incidences (cell, slot), at most 8 per node
+    if (!brick) {
       for (int q = tid; q < nn; q += TC_THREADS) {
         float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
         const int j0 = S.off[q], nj = S.off[q + 1] - j0;
