@@ -265,6 +265,8 @@ int sbx_update(sbx_ctx *ctx, double dt, double alpha);
  *                         SBX_MASS)
  *   SBX_LAYOUT_F32_NODE4  float [N][4] (x, y, z, unused): SBX_F_INT of
  *                         SBX_PREC_MIXED meshes; *len = 4 N
+ *   SBX_LAYOUT_F32_DOF    float per DOF and case: SBX_F_INT of batched
+ *                         SBX_PREC_FP32 meshes; *len = 3 N B
  * The address stays valid until the next mesh_upload or sbx_destroy; the
  * buffers behind SBX_U_N / SBX_U_NM1 swap roles every step, so ask again
  * after each step.  After writing U_n or U_{n-1} through the pointer, call
@@ -273,6 +275,7 @@ int sbx_update(sbx_ctx *ctx, double dt, double alpha);
  */
 #define SBX_LAYOUT_F64_DOF   0
 #define SBX_LAYOUT_F32_NODE4 1
+#define SBX_LAYOUT_F32_DOF   2
 int sbx_field_ptr(sbx_ctx *ctx, int which, void **ptr, int64_t *len, int *layout);
 
 /* sbx_touch: tell the library that U_n was changed through sbx_field_ptr

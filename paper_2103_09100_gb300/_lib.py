@@ -28,7 +28,7 @@ EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patte
            "read_field", "write_field", "sbx_profile", "sbx_query", "sbx_step_static",
            "set_modulus", "sbx_adjoint", "sbx_force", "sbx_update", "sbx_field_ptr", "sbx_touch",
            "sbx_set_mass"]
-SBX_LAYOUT_F64_DOF, SBX_LAYOUT_F32_NODE4 = 0, 1
+SBX_LAYOUT_F64_DOF, SBX_LAYOUT_F32_NODE4, SBX_LAYOUT_F32_DOF = 0, 1, 2
 SBX_Q_KERNELS_PER_STEP, SBX_Q_FORCE_LAUNCHES, SBX_Q_TILES, SBX_Q_BRICK_TILES = 0, 1, 2, 3
 SBX_STATIC_MAX_DOF = 4 * 1024 * 1024
 SBX_STATIC_MAX_PATTERNS = 144

@@ -6,14 +6,15 @@
 // Force kernel, one CTA (8 warps) per (tile of cells of one pattern, chunk
 // of 32 load cases); lane = load case:
 //   1. gather the tile's unique nodes (the 32 cases of each DOF form one
-//      coalesced 256-byte row); T = float: split each value into FP32 hi + lo
-//      once (bit operations), T = double: keep FP64;
+//      coalesced row); T = float: the (hi, lo) FP32 pairs of U_n that the
+//      update kernel wrote (hi + lo = U_n to ~2^-48), T = double: FP64;
 //   2. warp per cell: for j = 0..m-1, d_j = U(node) - U(slot-0 node) of this
 //      lane's case (K_p annihilates translations), transformed by the op
 //      (Sec. 3.2.2); acc(0..MM) += K_p(j, :) d_j with K_p rows read as float4
 //      broadcasts (K_p is symmetric, so row j is column j);
-//   3. E_e h_e Q^T acc is added into a per-tile accumulator in shared memory,
-//      then one coalesced FP64 atomic per (node, DOF, case) into f.
+//   3. E_e h_e Q^T acc goes straight to f with one atomic reduction per
+//      (cell, node DOF), coalesced over the warp's 32 cases (T = float: f is
+//      FP32; T = double: FP64).
 // T = float: FP32 contraction; T = double: FP64.  The update is FP64.
 #include <math.h>
 #include <string.h>
@@ -52,7 +53,7 @@ __host__ __device__ inline BRecLayout brec_layout(int ncell, int nn, int n) {
 }
 
 struct BSmem {
-  uint32_t K, u, f, rec, total;
+  uint32_t K, u, rec, total;
 };
 // mm: padded row length of K_p (a multiple of 4); tsz: sizeof(T)
 __host__ __device__ inline BSmem bsmem(int mm, int nn_max, int rec_max, uint32_t tsz) {
@@ -60,20 +61,16 @@ __host__ __device__ inline BSmem bsmem(int mm, int nn_max, int rec_max, uint32_t
   uint32_t o = 0;
   L.K = o;   o = b16(o + (uint32_t)mm * mm * tsz);
   L.u = o;   o = b16(o + (uint32_t)nn_max * 3u * BC * 8u);          // float2 or double
-  L.f = o;   o = b16(o + (uint32_t)nn_max * 3u * BC * tsz);
   L.rec = o; o = b16(o + (uint32_t)rec_max);
   L.total = o;
   return L;
 }
 
-__device__ __forceinline__ double to_f64(float x) { return f2d_bits(x); }
-__device__ __forceinline__ double to_f64(double x) { return x; }
-
 template <typename T, int MM>
 __global__ void __launch_bounds__(BT_THREADS, 2)
     k_force_batch(const TcTile *__restrict__ tiles, int nchunks, const uint8_t *__restrict__ recs,
                   const T *__restrict__ Kp, const int64_t *__restrict__ koff,
-                  const double *__restrict__ u, double *__restrict__ f, int B, LoadTable Ld,
+                  const void *__restrict__ uv, void *__restrict__ fv, int B, LoadTable Ld,
                   const int64_t *__restrict__ d_step, double dt, int nn_max, int rec_max) {
   extern __shared__ __align__(16) unsigned char smem[];
   const BSmem SL = bsmem(MM, nn_max, rec_max, sizeof(T));
@@ -95,7 +92,6 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
   const int32_t *nodes = reinterpret_cast<const int32_t *>(smem + SL.rec + R.nodes);
   const uint16_t *lid = reinterpret_cast<const uint16_t *>(smem + SL.rec + R.lid);
   T *Ks = reinterpret_cast<T *>(smem + SL.K);
-  T *fs = reinterpret_cast<T *>(smem + SL.f);
 
   // K_p, rows padded to MM with zeros (symmetric: row j = column j)
   for (int q = tid; q < m * MM; q += BT_THREADS) {
@@ -103,17 +99,17 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
     Ks[q] = i < m ? (T)Kp[koff[pat] + (int64_t)j * m + i] : (T)0;
   }
   const int b0 = chunk * BC;
-  for (int q = tid; q < nn * 3 * BC; q += BT_THREADS) {
-    const int nq = q / (3 * BC), a = (q / BC) % 3, b = q % BC;
-    const double x = u[(3 * (int64_t)nodes[nq] + a) * B + b0 + b];
-    if constexpr (sizeof(T) == 4) {
-      float hi, lo;
-      split_f64(x, hi, lo);
-      reinterpret_cast<float2 *>(smem + SL.u)[q] = make_float2(hi, lo);
-    } else {
-      reinterpret_cast<double *>(smem + SL.u)[q] = x;
-    }
-    fs[q] = (T)0;
+  // node rows of 32 cases: (node, dir) row t = 3 nq + a, 16-byte pieces
+  for (int q = tid; q < nn * 3 * (BC / 2); q += BT_THREADS) {
+    const int t = q >> 4, b = 2 * (q & 15);
+    const int nq = t / 3, a = t - 3 * nq;
+    const int64_t g = (3 * (int64_t)nodes[nq] + a) * B + b0 + b;
+    if constexpr (sizeof(T) == 4)
+      reinterpret_cast<float4 *>(smem + SL.u)[q] = *reinterpret_cast<const float4 *>(
+          reinterpret_cast<const float2 *>(uv) + g);
+    else
+      reinterpret_cast<double2 *>(smem + SL.u)[q] = *reinterpret_cast<const double2 *>(
+          reinterpret_cast<const double *>(uv) + g);
   }
   __syncthreads();
 
@@ -124,76 +120,129 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
     T acc[MM];
 #pragma unroll
     for (int i = 0; i < MM; ++i) acc[i] = (T)0;
-    for (int j = 0; j < m; ++j) {
-      const int k = j / 3, r = j - 3 * (j / 3);
-      const int a = r == 0 ? p0 : (r == 1 ? p1 : p2);
-      const int q = lid[k * ncell + c];
-      T d;
-      if constexpr (sizeof(T) == 4) {
-        const float2 *uu = reinterpret_cast<const float2 *>(smem + SL.u);
-        const float2 v = uu[(q * 3 + a) * BC + lane], v0 = uu[(q0 * 3 + a) * BC + lane];
-        d = (v.x - v0.x) + (v.y - v0.y);
-      } else {
-        const double *uu = reinterpret_cast<const double *>(smem + SL.u);
-        d = uu[(q * 3 + a) * BC + lane] - uu[(q0 * 3 + a) * BC + lane];
-      }
-      if ((op >> r) & 1) d = -d;
-      const T *kr = Ks + j * MM;
+    if constexpr (MM <= 24) {
+      // this lane's case: all differences d_j first (registers), then the
+      // contraction with K_p rows as float4 broadcasts
+      T d[MM];
 #pragma unroll
-      for (int i = 0; i < MM; i += 4) {
+      for (int k = 0; k < MM / 3; ++k) {
+        const int q = k < n ? lid[k * ncell + c] : q0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int a = r == 0 ? p0 : (r == 1 ? p1 : p2);
+          T x;
+          if constexpr (sizeof(T) == 4) {
+            const float2 *uu = reinterpret_cast<const float2 *>(smem + SL.u);
+            const float2 v = uu[(q * 3 + a) * BC + lane], v0 = uu[(q0 * 3 + a) * BC + lane];
+            x = (v.x - v0.x) + (v.y - v0.y);
+          } else {
+            const double *uu = reinterpret_cast<const double *>(smem + SL.u);
+            x = uu[(q * 3 + a) * BC + lane] - uu[(q0 * 3 + a) * BC + lane];
+          }
+          d[3 * k + r] = ((op >> r) & 1) ? -x : x;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < MM; ++j) {
+        if (j < m) {
+          const T *kr = Ks + j * MM;
+#pragma unroll
+          for (int i = 0; i < MM; i += 4) {
+            if constexpr (sizeof(T) == 4) {
+              const float4 kv = *reinterpret_cast<const float4 *>(kr + i);
+              acc[i] += kv.x * d[j];
+              acc[i + 1] += kv.y * d[j];
+              acc[i + 2] += kv.z * d[j];
+              acc[i + 3] += kv.w * d[j];
+            } else {
+              acc[i] += kr[i] * d[j];
+              acc[i + 1] += kr[i + 1] * d[j];
+              acc[i + 2] += kr[i + 2] * d[j];
+              acc[i + 3] += kr[i + 3] * d[j];
+            }
+          }
+        }
+      }
+    } else {
+      for (int j = 0; j < m; ++j) {
+        const int k = j / 3, r = j - 3 * (j / 3);
+        const int a = r == 0 ? p0 : (r == 1 ? p1 : p2);
+        const int q = lid[k * ncell + c];
+        T dj;
         if constexpr (sizeof(T) == 4) {
-          const float4 kv = *reinterpret_cast<const float4 *>(kr + i);
-          acc[i] += kv.x * d;
-          acc[i + 1] += kv.y * d;
-          acc[i + 2] += kv.z * d;
-          acc[i + 3] += kv.w * d;
+          const float2 *uu = reinterpret_cast<const float2 *>(smem + SL.u);
+          const float2 v = uu[(q * 3 + a) * BC + lane], v0 = uu[(q0 * 3 + a) * BC + lane];
+          dj = (v.x - v0.x) + (v.y - v0.y);
         } else {
-          acc[i] += kr[i] * d;
-          acc[i + 1] += kr[i + 1] * d;
-          acc[i + 2] += kr[i + 2] * d;
-          acc[i + 3] += kr[i + 3] * d;
+          const double *uu = reinterpret_cast<const double *>(smem + SL.u);
+          dj = uu[(q * 3 + a) * BC + lane] - uu[(q0 * 3 + a) * BC + lane];
+        }
+        if ((op >> r) & 1) dj = -dj;
+        const T *kr = Ks + j * MM;
+#pragma unroll
+        for (int i = 0; i < MM; i += 4) {
+          if constexpr (sizeof(T) == 4) {
+            const float4 kv = *reinterpret_cast<const float4 *>(kr + i);
+            acc[i] += kv.x * dj;
+            acc[i + 1] += kv.y * dj;
+            acc[i + 2] += kv.z * dj;
+            acc[i + 3] += kv.w * dj;
+          } else {
+            acc[i] += kr[i] * dj;
+            acc[i + 1] += kr[i + 1] * dj;
+            acc[i + 2] += kr[i + 2] * dj;
+            acc[i + 3] += kr[i + 3] * dj;
+          }
         }
       }
     }
     const T s = (T)scale[c];
+    T *f = reinterpret_cast<T *>(fv);
 #pragma unroll
     for (int i = 0; i < MM; ++i) {
       if (i < m) {
         const int k = i / 3, r = i % 3;
         const int a = r == 0 ? p0 : (r == 1 ? p1 : p2);
         const T v = ((op >> r) & 1) ? -s * acc[i] : s * acc[i];
-        atomicAdd(&fs[(lid[k * ncell + c] * 3 + a) * BC + lane], v);
+        atomicAdd(&f[(3 * (int64_t)nodes[lid[k * ncell + c]] + a) * B + b0 + lane], v);
       }
     }
   }
-  __syncthreads();
-  for (int q = tid; q < nn * 3 * BC; q += BT_THREADS) {
-    const int nq = q / (3 * BC), a = (q / BC) % 3, b = q % BC;
-    atomicAdd(&f[(3 * (int64_t)nodes[nq] + a) * B + b0 + b], to_f64(fs[q]));
-  }
+  T *f = reinterpret_cast<T *>(fv);
   if (blockIdx.x == 0 && Ld.n > 0) {
     const double t = (double)(*d_step) * dt;
     for (int l = tid; l < Ld.n; l += BT_THREADS)
-      atomicAdd(&f[Ld.dof[l]], -Ld.amp[l] * wavelet_value(Ld.kind[l], t, Ld.t1[l], Ld.ncyc[l]));
+      atomicAdd(&f[Ld.dof[l]], (T)(-Ld.amp[l] * wavelet_value(Ld.kind[l], t, Ld.t1[l], Ld.ncyc[l])));
   }
 }
 
 // U_{n+1} = -w f + 2 U_n - U_{n-1} (undamped) or the damped form; w per DOF,
-// f and U per (DOF, case); FP64.
-template <bool DAMPED>
+// f and U per (DOF, case); FP64.  F32: f is FP32 (widened by bit
+// re-packing) and U_{n+1} is also written as its (hi, lo) FP32 pair.
+template <bool DAMPED, bool F32>
 __global__ void __launch_bounds__(256)
-    k_update_batch(int64_t nd, int B, const double *__restrict__ w, double *__restrict__ f,
-                   const double *__restrict__ uc, double *__restrict__ up, double a, double b,
-                   int zero_f, int32_t *flags, int64_t *d_step) {
+    k_update_batch(int64_t nd, int B, const double *__restrict__ w, void *__restrict__ fv,
+                   const double *__restrict__ uc, double *__restrict__ up,
+                   float2 *__restrict__ pairs, double a, double b, int zero_f, int32_t *flags,
+                   int64_t *d_step) {
   bool bad = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double wv = w[i / B];
-    const double r = DAMPED ? fma(-wv, f[i], fma(a, uc[i], -b * up[i]))
-                            : fma(-wv, f[i], fma(2.0, uc[i], -up[i]));
+    const double fi = F32 ? f2d_bits(reinterpret_cast<const float *>(fv)[i])
+                          : reinterpret_cast<const double *>(fv)[i];
+    const double r = DAMPED ? fma(-wv, fi, fma(a, uc[i], -b * up[i]))
+                            : fma(-wv, fi, fma(2.0, uc[i], -up[i]));
     bad |= ((__double_as_longlong(r) >> 52) & 0x7FF) == 0x7FF;
     up[i] = r;
-    if (zero_f) f[i] = 0.0;
+    if (F32) {
+      float h, l;
+      split_f64(r, h, l);
+      pairs[i] = make_float2(h, l);
+      if (zero_f) reinterpret_cast<float *>(fv)[i] = 0.0f;
+    } else if (zero_f) {
+      reinterpret_cast<double *>(fv)[i] = 0.0;
+    }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 1);
   if (blockIdx.x == 0 && threadIdx.x == 0) *d_step += 1;
@@ -308,7 +357,7 @@ cudaError_t prepare_batch_kernels() {
 }
 
 template <typename T>
-static void launch_class(const sbx_ctx *ctx, int c, const T *K, const double *u, double *f,
+static void launch_class(const sbx_ctx *ctx, int c, const T *K, const void *u, void *f,
                          LoadTable L, double dt, cudaStream_t s) {
   const int nchunks = ctx->B / BC;
   const unsigned grid = (unsigned)ctx->n_b_tiles[c] * (unsigned)nchunks;
@@ -324,7 +373,7 @@ static void launch_class(const sbx_ctx *ctx, int c, const T *K, const double *u,
 #undef SBX_LAUNCH
 }
 
-cudaError_t launch_force_batch(const sbx_ctx *ctx, const double *u, double *f, double dt,
+cudaError_t launch_force_batch(const sbx_ctx *ctx, const void *u, void *f, double dt,
                                cudaStream_t s) {
   bool load_done = false;
   for (int c = 0; c < 3; ++c) {
@@ -340,18 +389,26 @@ cudaError_t launch_force_batch(const sbx_ctx *ctx, const double *u, double *f, d
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_batch(const sbx_ctx *ctx, const double *uc, double *up, double *f,
-                                double dt, double alpha, int zero_f, cudaStream_t s) {
+cudaError_t launch_update_batch(const sbx_ctx *ctx, const double *uc, double *up, void *f,
+                                float *pairs_out, double dt, double alpha, int zero_f,
+                                cudaStream_t s) {
   const int64_t nd = ctx->ndof * ctx->B;
   const double cm = 1.0 - 0.5 * alpha * dt, cp = 1.0 + 0.5 * alpha * dt;
   const int64_t want = (nd + 255) / 256;
   const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), 152 * 8);
-  if (alpha == 0.0)
-    k_update_batch<false><<<grid, 256, 0, s>>>(nd, ctx->B, ctx->d_w, f, uc, up, 2.0, 1.0, zero_f,
-                                               ctx->d_flags, ctx->d_step);
-  else
-    k_update_batch<true><<<grid, 256, 0, s>>>(nd, ctx->B, ctx->d_w, f, uc, up, 2.0 / cp, cm / cp,
-                                              zero_f, ctx->d_flags, ctx->d_step);
+  const double a = alpha == 0.0 ? 2.0 : 2.0 / cp, b = alpha == 0.0 ? 1.0 : cm / cp;
+  float2 *pr = reinterpret_cast<float2 *>(pairs_out);
+#define SBX_UPD(D, F)                                                                          \
+  k_update_batch<D, F><<<grid, 256, 0, s>>>(nd, ctx->B, ctx->d_w, f, uc, up, pr, a, b, zero_f, \
+                                            ctx->d_flags, ctx->d_step)
+  if (pairs_out) {
+    if (alpha == 0.0) SBX_UPD(false, true);
+    else SBX_UPD(true, true);
+  } else {
+    if (alpha == 0.0) SBX_UPD(false, false);
+    else SBX_UPD(true, false);
+  }
+#undef SBX_UPD
   return cudaGetLastError();
 }
 

@@ -272,6 +272,21 @@ __global__ void __launch_bounds__(256) k_update_f32(int64_t nn, const double *__
   if (blockIdx.x == 0 && threadIdx.x == 0) *d_step += 1;
 }
 
+__global__ void k_split_flat(int64_t nv, const double *u, float2 *pairs) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float h, l;
+    split_f64(u[i], h, l);
+    pairs[i] = make_float2(h, l);
+  }
+}
+
+__global__ void k_widen_flat(int64_t nv, const float *f, double *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = f2d_bits(f[i]);
+}
+
 __global__ void k_split_pairs(int64_t nn, const double *u, float *pairs) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -338,13 +353,23 @@ cudaError_t launch_update_f32(const sbx_ctx *ctx, const double *uc, double *up, 
 }
 
 cudaError_t launch_split_pairs(const sbx_ctx *ctx, const double *u, float *pairs, cudaStream_t s) {
-  k_split_pairs<<<update_grid(2 * ctx->N), 256, 0, s>>>(ctx->N, u, pairs);
+  if (ctx->B > 1) {
+    const int64_t nv = ctx->ndof * ctx->B;
+    k_split_flat<<<update_grid(nv), 256, 0, s>>>(nv, u, reinterpret_cast<float2 *>(pairs));
+  } else {
+    k_split_pairs<<<update_grid(2 * ctx->N), 256, 0, s>>>(ctx->N, u, pairs);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_widen_f32(const sbx_ctx *ctx, const float *f4, double *out, cudaStream_t s) {
-  k_widen_f32<<<update_grid(2 * ctx->N), 256, 0, s>>>(
-      ctx->N, reinterpret_cast<const float4 *>(f4), out);
+  if (ctx->B > 1) {
+    const int64_t nv = ctx->ndof * ctx->B;
+    k_widen_flat<<<update_grid(nv), 256, 0, s>>>(nv, f4, out);
+  } else {
+    k_widen_f32<<<update_grid(2 * ctx->N), 256, 0, s>>>(
+        ctx->N, reinterpret_cast<const float4 *>(f4), out);
+  }
   return cudaGetLastError();
 }
 

@@ -143,16 +143,21 @@ int set_device(sbx_ctx *ctx) {
 }
 
 int force(sbx_ctx *ctx, const double *u, double *f, double dt) {
-  if (ctx->B > 1) {
-    CK(sbx::launch_force_batch(ctx, u, f, dt, ctx->stream));
-  } else if (ctx->prec == SBX_PREC_MIXED) {
+  const float *pairs = nullptr;
+  if (ctx->uses_pairs()) {
     const int p = u == ctx->d_u[0] ? 0 : (u == ctx->d_u[1] ? 1 : -1);
-    if (p < 0) return fail(ctx, SBX_EINVAL, "the mixed force runs on the state buffers only");
+    if (p < 0) return fail(ctx, SBX_EINVAL, "this form's force runs on the state buffers only");
     if (!ctx->pair_valid[p]) {
       CK(sbx::launch_split_pairs(ctx, u, ctx->d_pair[p], ctx->stream));
       ctx->pair_valid[p] = true;
     }
-    CK(sbx::launch_force_tc(ctx, ctx->d_pair[p], reinterpret_cast<float *>(f), dt, ctx->stream));
+    pairs = ctx->d_pair[p];
+  }
+  if (ctx->B > 1) {
+    CK(sbx::launch_force_batch(ctx, pairs ? (const void *)pairs : (const void *)u, f, dt,
+                               ctx->stream));
+  } else if (ctx->prec == SBX_PREC_MIXED) {
+    CK(sbx::launch_force_tc(ctx, pairs, reinterpret_cast<float *>(f), dt, ctx->stream));
   } else {
     CK(sbx::launch_force_simt(ctx, u, f, dt, ctx->stream));
   }
@@ -161,7 +166,10 @@ int force(sbx_ctx *ctx, const double *u, double *f, double dt) {
 
 int update(sbx_ctx *ctx, const double *uc, double *up, double dt, double alpha, int zero_f) {
   if (ctx->B > 1) {
-    CK(sbx::launch_update_batch(ctx, uc, up, ctx->d_f, dt, alpha, zero_f, ctx->stream));
+    const int p = up == ctx->d_u[0] ? 0 : 1;
+    float *pairs_out = ctx->uses_pairs() ? ctx->d_pair[p] : nullptr;
+    CK(sbx::launch_update_batch(ctx, uc, up, ctx->d_f, pairs_out, dt, alpha, zero_f, ctx->stream));
+    if (pairs_out) ctx->pair_valid[p] = true;
   } else if (ctx->prec == SBX_PREC_MIXED) {
     const int p = up == ctx->d_u[0] ? 0 : 1;
     CK(sbx::launch_update_f32(ctx, uc, up, reinterpret_cast<float *>(ctx->d_f), ctx->d_pair[p], dt,
@@ -176,7 +184,7 @@ int update(sbx_ctx *ctx, const double *uc, double *up, double dt, double alpha, 
 // Mixed form: make the (hi, lo) pairs of U_n current before replaying a
 // graph (the captured steps take them from the previous update).
 int ensure_pairs(sbx_ctx *ctx) {
-  if (ctx->prec != SBX_PREC_MIXED || ctx->B != 1 || ctx->pair_valid[ctx->cur]) return SBX_OK;
+  if (!ctx->uses_pairs() || ctx->pair_valid[ctx->cur]) return SBX_OK;
   CK(sbx::launch_split_pairs(ctx, ctx->d_u[ctx->cur], ctx->d_pair[ctx->cur], ctx->stream));
   ctx->pair_valid[ctx->cur] = true;
   return SBX_OK;
@@ -469,9 +477,12 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   if (!rc) rc = dalloc(ctx, &ctx->d_u[1], nfield);
   if (!rc) rc = dalloc(ctx, &ctx->d_f, nfield);
   if (!rc) rc = dalloc(ctx, &ctx->d_w, ndof);
-  if (!rc && precision_mode == SBX_PREC_MIXED && n_rhs == 1) rc = dalloc(ctx, &ctx->d_fx, ndof);
-  if (!rc && precision_mode == SBX_PREC_MIXED && n_rhs == 1) rc = dalloc(ctx, &ctx->d_pair[0], 2 * ndof);
-  if (!rc && precision_mode == SBX_PREC_MIXED && n_rhs == 1) rc = dalloc(ctx, &ctx->d_pair[1], 2 * ndof);
+  // (hi, lo) pairs and the FP64 copy of the FP32 force: 2 floats per DOF and case
+  const bool pairs = (precision_mode == SBX_PREC_MIXED && n_rhs == 1) ||
+                     (precision_mode == SBX_PREC_FP32 && n_rhs > 1);
+  if (!rc && pairs) rc = dalloc(ctx, &ctx->d_fx, nfield);
+  if (!rc && pairs) rc = dalloc(ctx, &ctx->d_pair[0], 2 * nfield);
+  if (!rc && pairs) rc = dalloc(ctx, &ctx->d_pair[1], 2 * nfield);
   if (rc) {
     free_mesh(ctx);
     return rc;
@@ -605,7 +616,7 @@ int set_initial(sbx_ctx *ctx, const double *u0, const double *v0, double dt, dou
   CK(cudaMemsetAsync(ctx->d_f, 0, bytes, ctx->stream));
   if (int rc = force(ctx, U0, ctx->d_f, dt)) return rc;
   const double *F0 = ctx->d_f;
-  if (ctx->prec == SBX_PREC_MIXED && ctx->B == 1) {
+  if (ctx->uses_pairs()) {
     CK(sbx::launch_widen_f32(ctx, reinterpret_cast<const float *>(ctx->d_f), ctx->d_fx,
                              ctx->stream));
     F0 = ctx->d_fx;
@@ -892,6 +903,8 @@ int sbx_field_ptr(sbx_ctx *ctx, int which, void **ptr, int64_t *len, int *layout
       if (ctx->prec == SBX_PREC_MIXED && ctx->B == 1) {
         *layout = SBX_LAYOUT_F32_NODE4;
         *len = 4 * ctx->N;
+      } else if (ctx->uses_pairs()) {
+        *layout = SBX_LAYOUT_F32_DOF;
       }
       break;
     case SBX_MASS: *ptr = ctx->d_mass; *len = ctx->ndof; break;
@@ -982,7 +995,7 @@ int read_field(sbx_ctx *ctx, int which, double *out, int64_t len) {
     case SBX_U_NM1: src = ctx->d_u[ctx->cur ^ 1]; break;
     case SBX_F_INT:
       src = ctx->d_f;
-      if (ctx->prec == SBX_PREC_MIXED && ctx->B == 1) {   // float [N][4] -> [3N]
+      if (ctx->uses_pairs()) {   // FP32 force -> FP64 per DOF (and case)
         CK(sbx::launch_widen_f32(ctx, reinterpret_cast<const float *>(ctx->d_f), ctx->d_fx,
                                  ctx->stream));
         src = ctx->d_fx;

@@ -154,6 +154,12 @@ struct sbx_ctx {
   sbx::LoadTable loads() const {
     return sbx::LoadTable{n_load, d_load_dof, d_load_amp, d_load_kind, d_load_t1, d_load_ncyc};
   }
+  // FP32-contraction forms that take U_n as (hi, lo) pairs and keep f in
+  // FP32: the mixed form (one load case; pairs float [N][6], f float [N][4])
+  // and the batched FP32 form (pairs float2 and f float per DOF and case)
+  bool uses_pairs() const {
+    return (prec == SBX_PREC_MIXED && B == 1) || (prec == SBX_PREC_FP32 && B > 1);
+  }
 };
 
 namespace sbx {
@@ -194,10 +200,13 @@ int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vecto
                 const std::vector<double> &scale_sorted, const std::vector<int64_t> &start,
                 std::string &err);
 cudaError_t prepare_batch_kernels();
-cudaError_t launch_force_batch(const sbx_ctx *ctx, const double *u, double *f, double dt,
+// u: FP64 state (SBX_PREC_FP64) or the (hi, lo) pairs (SBX_PREC_FP32); f:
+// double or float per DOF and case
+cudaError_t launch_force_batch(const sbx_ctx *ctx, const void *u, void *f, double dt,
                                cudaStream_t s);
-cudaError_t launch_update_batch(const sbx_ctx *ctx, const double *uc, double *up, double *f,
-                                double dt, double alpha, int zero_f, cudaStream_t s);
+cudaError_t launch_update_batch(const sbx_ctx *ctx, const double *uc, double *up, void *f,
+                                float *pairs_out, double dt, double alpha, int zero_f,
+                                cudaStream_t s);
 // Mixed form: f is float [N][4] (x, y, z, unused) in the d_f allocation;
 // U_n enters the force kernel as its (hi, lo) pairs, float [N][6].
 cudaError_t launch_force_tc(const sbx_ctx *ctx, const float *pairs, float *f4, double dt,
@@ -205,7 +214,9 @@ cudaError_t launch_force_tc(const sbx_ctx *ctx, const float *pairs, float *f4, d
 cudaError_t launch_update_f32(const sbx_ctx *ctx, const double *uc, double *up, float *f4,
                               float *pairs_out, double dt, double alpha, int zero_f,
                               cudaStream_t s);
+// (hi, lo) pairs of a state buffer in the layout of ctx's form
 cudaError_t launch_split_pairs(const sbx_ctx *ctx, const double *u, float *pairs, cudaStream_t s);
-// out[3 i + d] = f4[4 i + d] (FP64)
+// the FP32 force buffer as FP64 per DOF (and case): mixed out[3 i + d] =
+// f4[4 i + d]; batched out[i] = f[i]
 cudaError_t launch_widen_f32(const sbx_ctx *ctx, const float *f4, double *out, cudaStream_t s);
 }  // namespace sbx
