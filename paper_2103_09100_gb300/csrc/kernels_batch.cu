@@ -66,6 +66,20 @@ __host__ __device__ inline BSmem bsmem(int mm, int nn_max, int rec_max, uint32_t
   return L;
 }
 
+// d = U(node q, dir a) - U(node q0, dir a) of this lane's case; FP32: from
+// the (hi, lo) pairs, (hi - hi_0) + (lo - lo_0)
+template <typename T>
+__device__ __forceinline__ T diff_of(const unsigned char *u, int q, int q0, int a, int lane) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 *uu = reinterpret_cast<const float2 *>(u);
+    const float2 v = uu[(q * 3 + a) * BC + lane], v0 = uu[(q0 * 3 + a) * BC + lane];
+    return (v.x - v0.x) + (v.y - v0.y);
+  } else {
+    const double *uu = reinterpret_cast<const double *>(u);
+    return uu[(q * 3 + a) * BC + lane] - uu[(q0 * 3 + a) * BC + lane];
+  }
+}
+
 template <typename T, int MM>
 __global__ void __launch_bounds__(BT_THREADS, 2)
     k_force_batch(const TcTile *__restrict__ tiles, int nchunks, const uint8_t *__restrict__ recs,
@@ -124,22 +138,23 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
       // this lane's case: all differences d_j first (registers), then the
       // contraction with K_p rows as float4 broadcasts
       T d[MM];
+      if (op == 0) {   // identity op (every 8-node cell): no component shuffle
 #pragma unroll
-      for (int k = 0; k < MM / 3; ++k) {
-        const int q = k < n ? lid[k * ncell + c] : q0;
+        for (int k = 0; k < MM / 3; ++k) {
+          const int q = k < n ? lid[k * ncell + c] : q0;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const int a = r == 0 ? p0 : (r == 1 ? p1 : p2);
-          T x;
-          if constexpr (sizeof(T) == 4) {
-            const float2 *uu = reinterpret_cast<const float2 *>(smem + SL.u);
-            const float2 v = uu[(q * 3 + a) * BC + lane], v0 = uu[(q0 * 3 + a) * BC + lane];
-            x = (v.x - v0.x) + (v.y - v0.y);
-          } else {
-            const double *uu = reinterpret_cast<const double *>(smem + SL.u);
-            x = uu[(q * 3 + a) * BC + lane] - uu[(q0 * 3 + a) * BC + lane];
+          for (int a = 0; a < 3; ++a) d[3 * k + a] = diff_of<T>(smem + SL.u, q, q0, a, lane);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < MM / 3; ++k) {
+          const int q = k < n ? lid[k * ncell + c] : q0;
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const int a = r == 0 ? p0 : (r == 1 ? p1 : p2);
+            const T x = diff_of<T>(smem + SL.u, q, q0, a, lane);
+            d[3 * k + r] = ((op >> r) & 1) ? -x : x;
           }
-          d[3 * k + r] = ((op >> r) & 1) ? -x : x;
         }
       }
 #pragma unroll
@@ -267,8 +282,8 @@ int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vecto
     const int np = ctx->pat_nodes[p], m = 3 * np, cls = class_of(m);
     int64_t c0 = 0;
     while (c0 < cnt[p]) {
-      // largest tile (16 cells or fewer) whose staging fits the target
-      int nc = (int)std::min<int64_t>(16, cnt[p] - c0);
+      // largest tile (32 cells or fewer) whose staging fits the target
+      int nc = (int)std::min<int64_t>(32, cnt[p] - c0);
       std::vector<int32_t> nodes;
       std::vector<uint16_t> lid;
       for (;;) {
