@@ -9,7 +9,9 @@ term, lumped-mass central-difference update.  Three forms are measured:
 * ``forms.fp64``: the plain FP64 form on the same mesh;
 * ``forms.batched``: 64 load cases per launch (FP32 contraction, FP64
   history) on the multi-point octree (levels 3-7, ~200k cells); its unit is
-  DOF·load-case·steps/s.
+  DOF·load-case·steps/s;
+* ``forms.trench_mixed``: the mixed form on the layered-trench octree
+  (levels 5-10, ~9.5M cells, ~32M DOF), 500 steps, with its device memory.
 
 Each form states its relative L2 error against the FP64 oracle after the
 same number of steps from the same start.
@@ -342,6 +344,21 @@ def main():
                             "rel_err_vs_oracle_max": max(errs), "err_cases": [0, 37],
                             "err_steps": nb_err}
         Bs.close()
+        # config 4: the layered-trench octree (~9.5M cells), mixed, 500 steps
+        mt = og.config_layered_trench()
+        free0, _ = torch.cuda.mem_get_info(local)
+        T = Solver.from_mesh(mt, precision="mixed", device=local, stream=stream.cuda_stream)
+        free1, _ = torch.cuda.mem_get_info(local)
+        T.initial()
+        T.step(3)
+        kt = 500
+        mst = time_steps(T, stream, kt, world, torch)
+        forms["trench_mixed"] = {"value": world * mt.n_dof * kt / (mst * 1e-3), "unit": UNIT,
+                                 "ms_per_step": mst / kt, "steps": kt,
+                                 "workload": mt.name + " (%d cells, %d DOF, %d patterns)"
+                                 % (mt.n_cells, mt.n_dof, len(T.masters)),
+                                 "device_memory_gb": (free0 - free1) / 1e9}
+        T.close()
         out["forms"] = forms
         out["rel_err_vs_oracle"] = forms[args.precision]["rel_err_vs_oracle"]
     else:
