@@ -108,3 +108,23 @@ def test_batched_rejects_bad_sizes():
         Solver.from_mesh(m, precision="fp32", n_rhs=20)
     with pytest.raises(L.SbxError):
         Solver.from_mesh(m, precision="mixed", n_rhs=32)
+
+
+def test_batched_fp32_damped_and_force_readback():
+    # damped batched FP32 update and the FP32 force read back as FP64
+    m = _with_sources(og.config_corner_cube(), 32, 9, t1_scale=10.0)
+    alpha = 0.4
+    P0 = cdm.make_problem(m, rhs=0, alpha=alpha)
+    S = Solver.from_mesh(m, precision="fp32", n_rhs=32, dt=P0.dt, alpha=alpha)
+    S.initial()
+    S.step(200)
+    g = S.field(L.SBX_U_N).reshape(-1, 32)
+    fg = S.field(L.SBX_F_INT).reshape(-1, 32)
+    for b in (0, 13, 31):
+        P = cdm.make_problem(m, dt=P0.dt, rhs=b, alpha=alpha)
+        u, up = cdm.initial_state(P)
+        u, up, _, f = cdm.run(P, 200, u, up, threads=4, want_force=True)
+        assert np.linalg.norm(g[:, b] - u) / np.linalg.norm(u) < 1e-5
+        # the oracle returns R_ext - R_int of the last step, the library R_int - R_ext
+        assert np.linalg.norm(fg[:, b] + f) / np.linalg.norm(f) < 1e-4
+    S.close()

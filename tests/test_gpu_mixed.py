@@ -119,3 +119,52 @@ def test_mixed_brick_and_list_tiles_cavity_counts():
     nb = L.sbx_query(S.ctx, L.SBX_Q_BRICK_TILES)
     print("receiver cube: %d brick tiles of %d tensor-core + SIMT tiles" % (nb, L.sbx_query(S.ctx, L.SBX_Q_TILES)))
     assert nb > 0
+
+
+def _mixed_vs_oracle(m, n_steps, alpha=0.0, u0=None, v0=None, threads=4):
+    P = cdm.make_problem(m, alpha=alpha)
+    S = Solver.from_mesh(m, precision="mixed", dt=P.dt, alpha=alpha)
+    S.initial(u0, v0)
+    S.step(n_steps)
+    u, up = cdm.initial_state(P, u0, v0)
+    u, up, _, _ = cdm.run(P, n_steps, u, up, threads=threads)
+    e = (rel(S.field(L.SBX_U_N), u), rel(S.field(L.SBX_U_NM1), up))
+    S.close()
+    return e
+
+
+def test_mixed_single_cell_no_loads():
+    m = og.small_uniform(1)
+    m.sources = []
+    u0 = np.random.default_rng(21).standard_normal(m.n_dof)
+    e = _mixed_vs_oracle(m, 40, u0=u0, threads=1)
+    assert max(e) < 1e-5, e
+
+
+def test_mixed_damped_with_initial_velocity():
+    # damped update (alpha > 0) and the Eq. D0 start with U_0, V_0 != 0
+    m = og.config_corner_cube()
+    rng = np.random.default_rng(22)
+    u0 = rng.standard_normal(m.n_dof) * 1e-3
+    v0 = rng.standard_normal(m.n_dof) * 1e-3
+    e = _mixed_vs_oracle(m, 300, alpha=0.3, u0=u0, v0=v0)
+    print("corner cube mixed, alpha 0.3, U_0 and V_0 given, 300 steps: %.3e %.3e" % e)
+    assert max(e) < 1e-5, e
+
+
+@pytest.mark.parametrize("n_steps", [1, 31, 32, 33, 65])
+def test_mixed_split_step_and_graphs_agree(n_steps):
+    # step_n (graph replay for runs of 32) = sbx_force + sbx_update per step,
+    # bit for bit up to the reduction order of the atomics
+    m = og.config_corner_cube()
+    A = Solver.from_mesh(m, precision="mixed")
+    B = Solver.from_mesh(m, precision="mixed", dt=A.dt)
+    A.initial()
+    B.initial()
+    A.step(n_steps)
+    for _ in range(n_steps):
+        L.sbx_force(B.ctx, B.dt)
+        L.sbx_update(B.ctx, B.dt)
+    ua, ub = A.field(), B.field()
+    assert rel(ub, ua) < 1e-6
+    assert L.sbx_get_step(A.ctx) == L.sbx_get_step(B.ctx) == n_steps
