@@ -45,8 +45,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one force launch pair on the cavity cube, from
 # the ncu capture summarised in profiles/k_force_tc_mixed_cavity_cube.md
-# (k_force_tc 96.7 MB + k_force_gen 13.1 MB); valid for that kernel version
-FORCE_TRAFFIC_MIXED = 109.8e6
+# (k_force_tc 67.5 MB + k_force_gen 13.1 MB); valid for that kernel version
+FORCE_TRAFFIC_MIXED = 80.6e6
 
 
 def dist_env():
@@ -185,6 +185,28 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batched_only(args):
+    """The batched form alone (64 load cases, multi-point octree)."""
+    import torch
+    import octree_gen as og
+    from paper_2103_09100_gb300 import Solver, _lib as L, build
+    build.build()
+    mb = og.config_multi_point()
+    B = 64
+    stream = torch.cuda.Stream()
+    S = Solver.from_mesh(mb, precision="fp32", n_rhs=B, stream=stream.cuda_stream)
+    S.initial()
+    S.step(args.warmup)
+    ms = time_steps(S, stream, args.only_batched, 1, torch)
+    ms_f, ms_u = L.sbx_profile(S.ctx, 20, S.dt, S.alpha)
+    print(json.dumps({"form": "batched", "value": mb.n_dof * B * args.only_batched / (ms * 1e-3),
+                      "unit": "DOF*load_cases*steps/s", "ms_per_step": ms / args.only_batched,
+                      "force_ms": ms_f / 20, "update_ms": ms_u / 20,
+                      "workload": "%s (%d cells, %d DOF), B = %d" % (mb.name, mb.n_cells, mb.n_dof, B)}),
+          flush=True)
+    S.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,6 +220,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the extra forms (fp64 / batched) and the error runs")
+    ap.add_argument("--only-batched", type=int, default=0, metavar="STEPS",
+                    help="diagnostics: time only the batched form for STEPS steps "
+                         "(its own JSON line; for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -205,6 +230,8 @@ def main():
         args.steps = 20 if args.impl == "reference" else (2000 if args.precision == "fp64" else 20000)
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_batched:
+        return run_batched_only(args)
 
     rank, world, local = dist_env()
     import torch
