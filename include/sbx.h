@@ -278,6 +278,20 @@ int sbx_update(sbx_ctx *ctx, double dt, double alpha);
 #define SBX_LAYOUT_F32_DOF   2
 int sbx_field_ptr(sbx_ctx *ctx, int which, void **ptr, int64_t *len, int *layout);
 
+/*
+ * sbx_wait_selftest: diagnostics of the failure path (the paper has no
+ * counterpart).  Every wait of the tensor-core kernels on an asynchronous
+ * completion (bulk copy, MMA) is bounded; a wait that gives up sets a device
+ * flag that the next synchronising call reports as SBX_ETIMEOUT, and the
+ * kernel returns instead of hanging.  This call runs that wait on a fresh
+ * barrier for at most `polls` polls (1 .. 2^30): with arrive = 1 the barrier
+ * completes first (returns SBX_OK), with arrive = 0 nothing completes it
+ * (returns SBX_ETIMEOUT).  The context's flags are left as they were and the
+ * context stays usable.  Synchronises the stream.
+ *   Errors: SBX_EINVAL (polls), SBX_ECUDA, SBX_ETIMEOUT as described.
+ */
+int sbx_wait_selftest(sbx_ctx *ctx, int64_t polls, int arrive);
+
 /* sbx_touch: tell the library that U_n was changed through sbx_field_ptr
  * (the mixed form re-derives its FP32 (hi, lo) split of U_n). */
 int sbx_touch(sbx_ctx *ctx);

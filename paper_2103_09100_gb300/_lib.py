@@ -27,7 +27,7 @@ EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patte
            "mesh_upload", "set_load", "set_initial", "step_n", "sbx_get_step", "sbx_set_step",
            "read_field", "write_field", "sbx_profile", "sbx_query", "sbx_step_static",
            "set_modulus", "sbx_adjoint", "sbx_force", "sbx_update", "sbx_field_ptr", "sbx_touch",
-           "sbx_set_mass"]
+           "sbx_set_mass", "sbx_wait_selftest"]
 SBX_LAYOUT_F64_DOF, SBX_LAYOUT_F32_NODE4, SBX_LAYOUT_F32_DOF = 0, 1, 2
 SBX_Q_KERNELS_PER_STEP, SBX_Q_FORCE_LAUNCHES, SBX_Q_TILES, SBX_Q_BRICK_TILES = 0, 1, 2, 3
 SBX_STATIC_MAX_DOF = 4 * 1024 * 1024
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH):
         "sbx_field_ptr": [vp, i32, C.POINTER(vp), C.POINTER(i64), C.POINTER(i32)],
         "sbx_touch": [vp],
         "sbx_set_mass": [vp, vp],
+        "sbx_wait_selftest": [vp, i64, i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -187,6 +188,10 @@ def sbx_field_ptr(ctx, which):
 
 def sbx_touch(ctx):
     _check(ctx, load().sbx_touch(ctx))
+
+
+def sbx_wait_selftest(ctx, polls, arrive):
+    _check(ctx, load().sbx_wait_selftest(ctx, int(polls), int(arrive)))
 
 
 def sbx_set_mass(ctx, mass):

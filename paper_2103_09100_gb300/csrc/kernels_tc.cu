@@ -528,6 +528,19 @@ __global__ void __launch_bounds__(256) k_force_gen(const Tile *__restrict__ tile
   }
 }
 
+// Self-test of the bounded completion wait every tensor-core kernel uses:
+// one thread waits on a fresh mbarrier (arrived on first when `arrive`),
+// giving up after `polls` polls; a give-up sets bit 2 of the flags, which
+// the host reports as SBX_ETIMEOUT.
+__global__ void k_wait_selftest(int32_t *flags, uint32_t polls, int arrive) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t mb = tc::smem_addr(&bar);
+  tc::mbar_init(mb, 1);
+  tc::mbar_fence_init();
+  if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+  if (!tc::mbar_wait_bounded(mb, 0u, polls)) atomicOr(flags, 2);
+}
+
 size_t gen_smem(int m) {
   return (size_t)(m * gen_mp(m) + GEN_TILE * gen_ds(m) + m * GEN_TILE) * sizeof(float);
 }
@@ -779,6 +792,11 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
     return SBX_ECUDA;
   }
   return SBX_OK;
+}
+
+cudaError_t launch_wait_selftest(const sbx_ctx *ctx, uint32_t polls, int arrive, cudaStream_t s) {
+  k_wait_selftest<<<1, 1, 0, s>>>(ctx->d_flags, polls, arrive);
+  return cudaGetLastError();
 }
 
 cudaError_t prepare_tc_kernels() {

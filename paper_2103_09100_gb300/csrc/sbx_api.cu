@@ -913,6 +913,24 @@ int sbx_field_ptr(sbx_ctx *ctx, int which, void **ptr, int64_t *len, int *layout
   return SBX_OK;
 }
 
+int sbx_wait_selftest(sbx_ctx *ctx, int64_t polls, int arrive) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (polls < 1 || polls > (int64_t)1 << 30) return fail(ctx, SBX_EINVAL, "polls out of range");
+  int32_t before = 0;
+  CK(cudaMemcpyAsync(&before, ctx->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(sbx::launch_wait_selftest(ctx, (uint32_t)polls, arrive, ctx->stream));
+  int32_t after = 0;
+  CK(cudaMemcpyAsync(&after, ctx->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  // leave the flags as they were
+  CK(cudaMemcpyAsync(ctx->d_flags, &before, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if ((after & 2) && !(before & 2)) return fail(ctx, SBX_ETIMEOUT, "the bounded wait gave up");
+  return SBX_OK;
+}
+
 int sbx_touch(sbx_ctx *ctx) {
   if (!ctx) return SBX_EINVAL;
   ctx->pair_valid[0] = ctx->pair_valid[1] = false;

@@ -194,6 +194,7 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
              const std::vector<uint8_t> &sym_sorted, const std::vector<double> &scale_sorted,
              std::string &err);
 cudaError_t prepare_tc_kernels();
+cudaError_t launch_wait_selftest(const sbx_ctx *ctx, uint32_t polls, int arrive, cudaStream_t s);
 // kernels_batch.cu
 int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<int64_t> &conn_off,
                 const std::vector<int64_t> &cnt, const std::vector<uint8_t> &sym_sorted,

@@ -264,3 +264,20 @@ def test_full_size_cavity_20_steps(cavity):
         e = rel(S.field(L.SBX_U_N), u)
         print("cavity %s 20-step rel error %.3e" % (prec, e))
         assert e < tol
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    # a wait that nothing completes gives up after its poll bound, the host
+    # sees SBX_ETIMEOUT, and the context keeps working (no GPU fault)
+    m = og.config_corner_cube()
+    P = cdm.make_problem(m)
+    S = _solver(m, P)
+    L.sbx_wait_selftest(S.ctx, 1000, 1)
+    with pytest.raises(L.SbxError) as e:
+        L.sbx_wait_selftest(S.ctx, 1000, 0)
+    assert e.value.code == L.SBX_ETIMEOUT
+    S.initial()
+    S.step(10)
+    u, up = cdm.initial_state(P)
+    u, _, _, _ = cdm.run(P, 10, u, up)
+    assert rel(S.field(L.SBX_U_N), u) < 1e-12
