@@ -212,3 +212,38 @@ def test_gloo_two_ranks_equal_global_oracle():
     ug = u.reshape(-1, 3)
     for r in res:
         assert np.abs(r["u"].reshape(-1, 3) - ug[r["nodes"]]).max() <= 1e-12 * np.abs(ug).max()
+
+
+def _rank_leaves(rank, world, port, out_dir):
+    # rank 1 leaves after set-up (between steps, nothing in flight); rank 0's
+    # next interface sum must fail with an error instead of hanging
+    import datetime
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank,
+                            world_size=world, timeout=datetime.timedelta(seconds=5))
+    m = _mesh()
+    parts = partition(m.slot_node, world, fixed_nodes=m.fixed_nodes, sources=m.sources)
+    e = OracleEngine(m, parts[rank])
+    nodecut.setup_distributed(e, 0.5)
+    status = "stepped"
+    if rank == 1:
+        status = "left"
+    else:
+        try:
+            nodecut.step_distributed(e, 5)
+        except Exception as exc:   # the peer is gone
+            status = "detected: %s" % type(exc).__name__
+    with open(os.path.join(out_dir, "r%d.txt" % rank), "w") as f:
+        f.write(status)
+    if rank == 0:
+        dist.destroy_process_group()
+
+
+def test_gloo_rank_leaving_is_detected():
+    mp = pytest.importorskip("torch.multiprocessing")
+    with tempfile.TemporaryDirectory() as d:
+        mp.spawn(_rank_leaves, args=(2, _free_port(), d), nprocs=2, join=True)
+        s0 = open(os.path.join(d, "r0.txt")).read()
+        s1 = open(os.path.join(d, "r1.txt")).read()
+    assert s1 == "left"
+    assert s0.startswith("detected"), s0
