@@ -14,8 +14,9 @@
 //                octree) on the 5th-generation tensor cores: a persistent,
 //                software-pipelined kernel over tiles of up to 128 cells.
 //                The record of tile i+2 streams in by one 1-D bulk copy (TMA
-//                engine, completion on an mbarrier) and tile i+1's node
-//                pairs by per-thread cp.async while tile i is computed.
+//                engine, completion on an mbarrier) while tile i is
+//                computed; tile i+1's node pairs follow by per-thread
+//                cp.async, issued while tile i's MMAs run.
 //                A (128 x 24) = the cells' differences rounded to TF32 hi +
 //                lo, written to tensor memory by tcgen05.st (row = cell =
 //                TMEM lane);  D (TMEM) = A_hi B_hi^T + A_hi B_lo^T + A_lo
@@ -250,17 +251,9 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
     const int next = tile + G;
     TcTile ahead;   // descriptor of tile i + 2 (thread 0), fetched early
     if (tid == 0 && next + G < ntiles) ahead = tiles[next + G];
-    // this tile's node pairs (own cp.async) and the next tile's record
+    // this tile's node pairs (own cp.async, issued during the previous tile)
     tc::cp_async_wait_all();
-    bool got = true;
-    if (next < ntiles) got = tc::mbar_wait_bounded(mb_rec0 + 8u * so, (ph_rec >> so) & 1u, WAIT_POLLS);
-    ok = __syncthreads_and(got);
-    if (!ok) break;
-    if (next < ntiles) {
-      ph_rec ^= 1u << so;
-      pend &= ~(1u << so);
-      issue_gather(s ^ 1);
-    }
+    __syncthreads();
     const Stage S = stage_view(stage_base(s), SL.u_off);
     const int ncell = S.hdr[1], nn = S.hdr[2];
     const bool brick = S.hdr[3] == 1;
@@ -323,10 +316,22 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
       }
       tc::mma_commit(mb_mma);
     }
-    ok = __syncthreads_and(tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_POLLS));
+    // while the MMAs run: the next tile's record (issued a tile ago) and
+    // the gather of its node pairs
+    bool got = true;
+    if (next < ntiles) {
+      got = tc::mbar_wait_bounded(mb_rec0 + 8u * so, (ph_rec >> so) & 1u, WAIT_POLLS);
+      if (got) issue_gather(s ^ 1);
+    }
+    got = tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_POLLS) && got;
+    ok = __syncthreads_and(got);
     tc::fence_after_sync();
     if (!ok) break;
     ph_mma ^= 1u;
+    if (next < ntiles) {
+      ph_rec ^= 1u << so;
+      pend &= ~(1u << so);
+    }
     // epilogue: warps w and w + 4 read TMEM lanes 32 (w % 4) .. + 31, columns
     // 12 h .. 12 h + 11 (cell, slots 4 h .. 4 h + 3) times E h
     {
