@@ -245,15 +245,20 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
   // thread (c, h): cell c (= TMEM lane) and its slots 4h .. 4h + 3
   const int fc = tid & 127, fh = tid >> 7;
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  TcTile ahead;   // descriptor of the tile after next (thread 0), fetched a tile early
   for (int i = 0; ok && tile < ntiles; ++i, tile += G) {
     const int s = i & 1;
     const uint32_t so = (uint32_t)(s ^ 1);
     const int next = tile + G;
-    TcTile ahead;   // descriptor of tile i + 2 (thread 0), fetched early
-    if (tid == 0 && next + G < ntiles) ahead = tiles[next + G];
     // this tile's node pairs (own cp.async, issued during the previous tile)
     tc::cp_async_wait_all();
     __syncthreads();
+    // every warp is past the previous tile: its stage takes the next record
+    if (i > 0 && next < ntiles) {
+      if (tid == 0) issue_record((int)so, ahead);
+      pend |= 1u << so;
+    }
+    if (tid == 0 && next + G < ntiles) ahead = tiles[next + G];
     const Stage S = stage_view(stage_base(s), SL.u_off);
     const int ncell = S.hdr[1], nn = S.hdr[2];
     const bool brick = S.hdr[3] == 1;
@@ -414,11 +419,6 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
         red_add_v4(f4 + 4 * (int64_t)S.nodes[q], a0, a1, a2);
       }
     }
-    __syncthreads();   // stage s and F are free
-    if (next + G < ntiles) {
-      if (tid == 0) issue_record(s, ahead);
-      pend |= 1u << s;
-    }
   }
   if (!ok) {
     if (tid == 0) atomicOr(flags, 2);
@@ -434,18 +434,22 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
 }
 
 // Cells of the other patterns: one tile (<= 32 cells of pattern p) per CTA.
-// D[c][j] (FP32 differences to slot 0, master frame; row stride ds),
+// K_p and the tile's node pairs arrive by cp.async (node ids loaded first,
+// all at once); D[c][j] (FP32 differences to slot 0, master frame; row
+// stride ds),
 // F[i][c] = E h sum_j K_p[i][j] D[c][j] with K_p rows padded to mp (a
 // multiple of 4).  Warp g owns rows g, g + 8, ..., lane = cell: per four j
 // one 16-byte load of D (conflict-free: ds / 4 is odd) serves up to ten
 // rows, each a broadcast 16-byte load of K_p and four FFMA.
 constexpr int GEN_RMAX = 10;   // rows per warp: ceil(78 / 8)
+constexpr int GEN_THREADS = 256;
+constexpr int GEN_Q = 4;       // (cell, slot) items per thread: 26 * 32 <= 4 * 256
 __host__ __device__ inline int gen_mp(int m) { return (m + 3) & ~3; }
 __host__ __device__ inline int gen_ds(int m) {
   const int mp = gen_mp(m);
   return ((mp >> 2) & 1) ? mp : mp + 4;
 }
-__global__ void __launch_bounds__(256) k_force_gen(const Tile *__restrict__ tiles, MeshView M,
+__global__ void __launch_bounds__(GEN_THREADS) k_force_gen(const Tile *__restrict__ tiles, MeshView M,
                                                    const float *__restrict__ Kpad,
                                                    const int64_t *__restrict__ kpoff,
                                                    const float *__restrict__ u,
@@ -460,24 +464,48 @@ __global__ void __launch_bounds__(256) k_force_gen(const Tile *__restrict__ tile
   float *Ks = reinterpret_cast<float *>(smem_g);   // [m][mp]
   float *D = Ks + m * mp;                         // [32][ds]
   float *F = D + GEN_TILE * ds;                   // [m][32]
+  float *U = F + m * GEN_TILE;                    // [n][32] node pairs (hi, lo), item k * 32 + c
   if (blockIdx.x == 0 && Ld.n > 0) add_loads(Ld, d_step, dt, f4);
   {   // K_p rows padded to mp in global memory (16-byte aligned per pattern)
-    const float4 *src = reinterpret_cast<const float4 *>(Kpad + kpoff[p]);
-    float4 *dst = reinterpret_cast<float4 *>(Ks);
-    for (int q = tid; q < (m * mp) >> 2; q += blockDim.x) dst[q] = src[q];
+    const float *src = Kpad + kpoff[p];
+    const uint32_t dst = tc::smem_addr(Ks);
+    for (int q = tid; q < (m * mp) >> 2; q += blockDim.x) tc::cp_async16(dst + 16u * q, src + 4 * q);
   }
-  if (lane < nc)   // zero the padding columns of D
-    for (int j = m + g; j < mp; j += 8) D[lane * ds + j] = 0.0f;
   const int64_t Cp = M.pat_ccount[p];
   const int32_t *cn = M.conn + M.conn_off[p] + t.cell0;
   const int64_t gbase = M.pat_cstart[p] + t.cell0;
+  // item w = k * 32 + c (slot k of cell c): node ids first (independent
+  // loads), then the node pairs by cp.async; the ids stay for the scatter
+  int32_t nodeq[GEN_Q];
+#pragma unroll
+  for (int q = 0; q < GEN_Q; ++q) {
+    const int w = tid + q * GEN_THREADS;
+    nodeq[q] = (w < n * GEN_TILE && (w & 31) < nc) ? cn[(int64_t)(w >> 5) * Cp + (w & 31)] : -1;
+  }
+  {
+    const uint32_t ub = tc::smem_addr(U);
+#pragma unroll
+    for (int q = 0; q < GEN_Q; ++q) {
+      if (nodeq[q] < 0) continue;
+      const uint32_t d = ub + 24u * (uint32_t)(tid + q * GEN_THREADS);
+      const float *src = u + 6 * (int64_t)nodeq[q];
+      tc::cp_async8(d, src);
+      tc::cp_async8(d + 8u, src + 2);
+      tc::cp_async8(d + 16u, src + 4);
+    }
+    tc::cp_async_commit();
+  }
+  if (lane < nc)   // zero the padding columns of D
+    for (int j = m + g; j < mp; j += 8) D[lane * ds + j] = 0.0f;
+  tc::cp_async_wait_all();
+  __syncthreads();
+  // D[c][3 k + r]: differences to slot 0 in the master frame
   for (int w = tid; w < n * GEN_TILE; w += blockDim.x) {
     const int k = w >> 5, c = w & 31;
     float x[3] = {0.0f, 0.0f, 0.0f};
     if (c < nc) {
-      const int32_t node = cn[(int64_t)k * Cp + c], ref = cn[c];
       float d[3];
-      node_diff(u + 6 * (int64_t)node, u + 6 * (int64_t)ref, d[0], d[1], d[2]);
+      node_diff(U + 6 * w, U + 6 * c, d[0], d[1], d[2]);
       const int op = M.sym[gbase + c];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
@@ -515,9 +543,11 @@ __global__ void __launch_bounds__(256) k_force_gen(const Tile *__restrict__ tile
   }
   __syncthreads();
   // back to the cell frame, f_cell[perm r] = sgn r f_master[r]
-  for (int w = tid; w < n * GEN_TILE; w += blockDim.x) {
+#pragma unroll
+  for (int q = 0; q < GEN_Q; ++q) {
+    const int w = tid + q * GEN_THREADS;
+    if (nodeq[q] < 0) continue;
     const int k = w >> 5, c = w & 31;
-    if (c >= nc) continue;
     const int op = M.sym[gbase + c];
     float y[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
@@ -529,7 +559,7 @@ __global__ void __launch_bounds__(256) k_force_gen(const Tile *__restrict__ tile
       y[1] += a == 1 ? sv : 0.0f;
       y[2] += a == 2 ? sv : 0.0f;
     }
-    red_add_v4(f4 + 4 * (int64_t)cn[(int64_t)k * Cp + c], y[0], y[1], y[2]);
+    red_add_v4(f4 + 4 * (int64_t)nodeq[q], y[0], y[1], y[2]);
   }
 }
 
@@ -547,7 +577,8 @@ __global__ void k_wait_selftest(int32_t *flags, uint32_t polls, int arrive) {
 }
 
 size_t gen_smem(int m) {
-  return (size_t)(m * gen_mp(m) + GEN_TILE * gen_ds(m) + m * GEN_TILE) * sizeof(float);
+  return (size_t)(m * gen_mp(m) + GEN_TILE * gen_ds(m) + m * GEN_TILE + 2 * m * GEN_TILE) *
+         sizeof(float);
 }
 
 float tf32_round_host(float x) {
@@ -836,7 +867,7 @@ cudaError_t launch_force_tc(const sbx_ctx *ctx, const float *pairs, float *f4, d
   }
   if (ctx->n_gen_tiles > 0) {
     cudaStream_t sg = both ? ctx->side : s;
-    k_force_gen<<<ctx->n_gen_tiles, 256, ctx->gen_smem, sg>>>(ctx->d_gen_tiles, ctx->view(),
+    k_force_gen<<<ctx->n_gen_tiles, GEN_THREADS, ctx->gen_smem, sg>>>(ctx->d_gen_tiles, ctx->view(),
                                                               ctx->d_gen_K, ctx->d_gen_koff,
                                                               pairs, f4, L, ctx->d_step, dt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
