@@ -449,6 +449,29 @@ __host__ __device__ inline int gen_ds(int m) {
   const int mp = gen_mp(m);
   return ((mp >> 2) & 1) ? mp : mp + 4;
 }
+// F[i][lane] = sc sum_j K_p[i][j] D[lane][j] for the rows i = g + 8 r, r < R
+// (the last group may run past m).
+template <int R>
+__device__ __forceinline__ void gen_contract(const float *Ks, const float *Dc, float *F, int mp,
+                                             int m, int g, int lane, float sc) {
+  float acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0.0f;
+  const bool last = g + 8 * (R - 1) < m;
+  for (int j = 0; j < mp; j += 4) {
+    const float4 x = *reinterpret_cast<const float4 *>(Dc + j);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r == R - 1 && !last) break;
+      const float4 k = *reinterpret_cast<const float4 *>(Ks + (g + 8 * r) * mp + j);
+      acc[r] = fmaf(k.x, x.x, fmaf(k.y, x.y, fmaf(k.z, x.z, fmaf(k.w, x.w, acc[r]))));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (g + 8 * r < m) F[(g + 8 * r) * GEN_TILE + lane] = sc * acc[r];
+}
+
 __global__ void __launch_bounds__(GEN_THREADS) k_force_gen(const Tile *__restrict__ tiles, MeshView M,
                                                    const float *__restrict__ Kpad,
                                                    const int64_t *__restrict__ kpoff,
@@ -519,26 +542,19 @@ __global__ void __launch_bounds__(GEN_THREADS) k_force_gen(const Tile *__restric
   }
   __syncthreads();
   {
-    float acc[GEN_RMAX];
-#pragma unroll
-    for (int r = 0; r < GEN_RMAX; ++r) acc[r] = 0.0f;
-    const float *Dc = D + lane * ds;
-    for (int j = 0; j < mp; j += 4) {
-      const float4 x = *reinterpret_cast<const float4 *>(Dc + j);
-#pragma unroll
-      for (int r = 0; r < GEN_RMAX; ++r) {
-        const int i = g + 8 * r;
-        if (i < m) {
-          const float4 k = *reinterpret_cast<const float4 *>(Ks + i * mp + j);
-          acc[r] = fmaf(k.x, x.x, fmaf(k.y, x.y, fmaf(k.z, x.z, fmaf(k.w, x.w, acc[r]))));
-        }
-      }
-    }
     const float sc = lane < nc ? (float)M.scale[gbase + lane] : 0.0f;
-#pragma unroll
-    for (int r = 0; r < GEN_RMAX; ++r) {
-      const int i = g + 8 * r;
-      if (i < m) F[i * GEN_TILE + lane] = sc * acc[r];
+    const float *Dc = D + lane * ds;
+    switch ((m + 7) >> 3) {   // rows per warp, so that no unrolled row is idle
+      case 1: gen_contract<1>(Ks, Dc, F, mp, m, g, lane, sc); break;
+      case 2: gen_contract<2>(Ks, Dc, F, mp, m, g, lane, sc); break;
+      case 3: gen_contract<3>(Ks, Dc, F, mp, m, g, lane, sc); break;
+      case 4: gen_contract<4>(Ks, Dc, F, mp, m, g, lane, sc); break;
+      case 5: gen_contract<5>(Ks, Dc, F, mp, m, g, lane, sc); break;
+      case 6: gen_contract<6>(Ks, Dc, F, mp, m, g, lane, sc); break;
+      case 7: gen_contract<7>(Ks, Dc, F, mp, m, g, lane, sc); break;
+      case 8: gen_contract<8>(Ks, Dc, F, mp, m, g, lane, sc); break;
+      case 9: gen_contract<9>(Ks, Dc, F, mp, m, g, lane, sc); break;
+      default: gen_contract<GEN_RMAX>(Ks, Dc, F, mp, m, g, lane, sc); break;
     }
   }
   __syncthreads();
