@@ -817,6 +817,12 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   if (int rc = up(&ctx->d_tc_K, Bhl)) return rc;
   if (int rc = up(&ctx->d_tc_rec, recs)) return rc;
   if (int rc = up(&ctx->d_tc_tiles[0], tiles)) return rc;
+  // largest patterns first (the CTAs are issued in order: long ones start
+  // early, short ones fill the end)
+  std::stable_sort(gen.begin(), gen.end(), [&](const Tile &a, const Tile &b) {
+    const int na = ctx->pat_nodes[a.pat], nb = ctx->pat_nodes[b.pat];
+    return na * na * a.ncell > nb * nb * b.ncell;   // ~ the tile's multiply-adds
+  });
   if (int rc = up(&ctx->d_gen_tiles, gen)) return rc;
   if (int rc = up(&ctx->d_gen_K, Kpad)) return rc;
   if (int rc = up(&ctx->d_gen_koff, kpoff)) return rc;
