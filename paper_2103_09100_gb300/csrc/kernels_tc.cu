@@ -499,6 +499,10 @@ __global__ void __launch_bounds__(GEN_THREADS) k_force_gen(const Tile *__restric
   const int64_t gbase = M.pat_cstart[p] + t.cell0;
   // item w = k * 32 + c (slot k of cell c): node ids first (independent
   // loads), then the node pairs by cp.async; the ids stay for the scatter
+  // the item's cell is c = w % 32 = lane for every q: its op and E h are
+  // loaded once, beside the node ids
+  const int op_c = lane < nc ? (int)M.sym[gbase + lane] : 0;
+  const float sc = lane < nc ? (float)M.scale[gbase + lane] : 0.0f;
   int32_t nodeq[GEN_Q];
 #pragma unroll
   for (int q = 0; q < GEN_Q; ++q) {
@@ -529,7 +533,7 @@ __global__ void __launch_bounds__(GEN_THREADS) k_force_gen(const Tile *__restric
     if (c < nc) {
       float d[3];
       node_diff(U + 6 * w, U + 6 * c, d[0], d[1], d[2]);
-      const int op = M.sym[gbase + c];
+      const int op = op_c;
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         const int a = op_perm_of(op, r);
@@ -542,7 +546,6 @@ __global__ void __launch_bounds__(GEN_THREADS) k_force_gen(const Tile *__restric
   }
   __syncthreads();
   {
-    const float sc = lane < nc ? (float)M.scale[gbase + lane] : 0.0f;
     const float *Dc = D + lane * ds;
     switch ((m + 7) >> 3) {   // rows per warp, so that no unrolled row is idle
       case 1: gen_contract<1>(Ks, Dc, F, mp, m, g, lane, sc); break;
@@ -564,7 +567,7 @@ __global__ void __launch_bounds__(GEN_THREADS) k_force_gen(const Tile *__restric
     const int w = tid + q * GEN_THREADS;
     if (nodeq[q] < 0) continue;
     const int k = w >> 5, c = w & 31;
-    const int op = M.sym[gbase + c];
+    const int op = op_c;
     float y[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
