@@ -45,8 +45,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one force launch pair on the cavity cube, from
 # the ncu capture summarised in profiles/k_force_tc_mixed_cavity_cube.md
-# (k_force_tc 67.5 MB + k_force_gen 13.1 MB); valid for that kernel version
-FORCE_TRAFFIC_MIXED = 80.6e6
+# (k_force_tc 67.6 MB + k_force_gen 13.1 MB); valid for that kernel version
+FORCE_TRAFFIC_MIXED = 80.7e6
 
 
 def dist_env():
