@@ -246,6 +246,9 @@ __device__ __forceinline__ void put_pair(float *p, double x0, double x1, double 
   q[2] = make_float2(l1, l2);
 }
 
+// UPD_U nodes per thread and round, all their loads issued before any
+// arithmetic (the update is bound by memory latency x parallelism).
+constexpr int UPD_U = 2;
 template <bool DAMPED>
 __global__ void __launch_bounds__(256) k_update_f32(int64_t nn, const double *__restrict__ w,
                                                     float4 *__restrict__ f,
@@ -254,19 +257,36 @@ __global__ void __launch_bounds__(256) k_update_f32(int64_t nn, const double *__
                                                     float *__restrict__ pairs, double a, double b,
                                                     int zero_f, int32_t *flags, int64_t *d_step) {
   bool bad = false;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float4 fv = f[i];
-    const int64_t o = 3 * i;
-    const double r0 = cdm_update<DAMPED>(w[o], f2d_bits(fv.x), uc[o], up[o], a, b);
-    const double r1 = cdm_update<DAMPED>(w[o + 1], f2d_bits(fv.y), uc[o + 1], up[o + 1], a, b);
-    const double r2 = cdm_update<DAMPED>(w[o + 2], f2d_bits(fv.z), uc[o + 2], up[o + 2], a, b);
-    bad |= nonfinite(r0) || nonfinite(r1) || nonfinite(r2);
-    up[o] = r0;
-    up[o + 1] = r1;
-    up[o + 2] = r2;
-    put_pair(pairs + 6 * i, r0, r1, r2);
-    if (zero_f) f[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < nn;
+       i0 += UPD_U * stride) {
+    float4 fv[UPD_U];
+    double wv[UPD_U][3], cv[UPD_U][3], pv[UPD_U][3];
+#pragma unroll
+    for (int q = 0; q < UPD_U; ++q) {
+      const int64_t i = i0 + q * stride < nn ? i0 + q * stride : i0;
+      fv[q] = f[i];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        wv[q][d] = w[3 * i + d];
+        cv[q][d] = uc[3 * i + d];
+        pv[q][d] = up[3 * i + d];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < UPD_U; ++q) {
+      const int64_t i = i0 + q * stride;
+      if (i >= nn) break;
+      const double r0 = cdm_update<DAMPED>(wv[q][0], f2d_bits(fv[q].x), cv[q][0], pv[q][0], a, b);
+      const double r1 = cdm_update<DAMPED>(wv[q][1], f2d_bits(fv[q].y), cv[q][1], pv[q][1], a, b);
+      const double r2 = cdm_update<DAMPED>(wv[q][2], f2d_bits(fv[q].z), cv[q][2], pv[q][2], a, b);
+      bad |= nonfinite(r0) || nonfinite(r1) || nonfinite(r2);
+      up[3 * i] = r0;
+      up[3 * i + 1] = r1;
+      up[3 * i + 2] = r2;
+      put_pair(pairs + 6 * i, r0, r1, r2);
+      if (zero_f) f[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 1);
   if (blockIdx.x == 0 && threadIdx.x == 0) *d_step += 1;
