@@ -297,6 +297,28 @@ int sbx_wait_selftest(sbx_ctx *ctx, int64_t polls, int arrive);
 int sbx_touch(sbx_ctx *ctx);
 
 /*
+ * sbx_set_receivers: record a time history of the displacement at n_rec
+ * entries of the state array (receivers, as in Sec. 5's measured
+ * responses) after every step that sbx_step_n takes from now on, for at
+ * most max_steps steps.  rec_idx[r] indexes the state array U_n of this
+ * context: DOF 3 node + d, batched (3 node + d) B + b; host or device
+ * pointer, copied.  n_rec = 0 turns recording off.  Recording costs one
+ * small kernel launch per step; it is captured with the step graphs.
+ *   Errors: SBX_ESTATE (no mesh), SBX_EINVAL (index out of range,
+ *   n_rec < 0, max_steps < 1), SBX_ENOMEM.
+ */
+int sbx_set_receivers(sbx_ctx *ctx, int64_t n_rec, const int64_t *rec_idx, int64_t max_steps);
+
+/*
+ * sbx_read_history: the recorded rows, out[s n_rec + r] = U at receiver r
+ * after the s-th step since sbx_set_receivers, for s < *n_rows =
+ * min(steps taken, max_steps, max_rows).  out: host or device pointer with
+ * room for max_rows n_rec doubles.  Synchronises the context's stream.
+ *   Errors: SBX_ESTATE (no receivers set), SBX_EINVAL (NULL, max_rows < 0).
+ */
+int sbx_read_history(sbx_ctx *ctx, double *out, int64_t max_rows, int64_t *n_rows);
+
+/*
  * sbx_set_mass: replace the lumped diagonal mass M_diag[3N] (Sec. 3.3) --
  * e.g. by the sum over all parts of a node-cut partition, whose interface
  * nodes receive mass from cells on several GPUs.  Values > 0; M^-1 stays 0

@@ -27,7 +27,7 @@ EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patte
            "mesh_upload", "set_load", "set_initial", "step_n", "sbx_get_step", "sbx_set_step",
            "read_field", "write_field", "sbx_profile", "sbx_query", "sbx_step_static",
            "set_modulus", "sbx_adjoint", "sbx_force", "sbx_update", "sbx_field_ptr", "sbx_touch",
-           "sbx_set_mass", "sbx_wait_selftest"]
+           "sbx_set_mass", "sbx_wait_selftest", "sbx_set_receivers", "sbx_read_history"]
 SBX_LAYOUT_F64_DOF, SBX_LAYOUT_F32_NODE4, SBX_LAYOUT_F32_DOF = 0, 1, 2
 SBX_Q_KERNELS_PER_STEP, SBX_Q_FORCE_LAUNCHES, SBX_Q_TILES, SBX_Q_BRICK_TILES = 0, 1, 2, 3
 SBX_STATIC_MAX_DOF = 4 * 1024 * 1024
@@ -76,6 +76,8 @@ def load(path: str = LIB_PATH):
         "sbx_touch": [vp],
         "sbx_set_mass": [vp, vp],
         "sbx_wait_selftest": [vp, i64, i32],
+        "sbx_set_receivers": [vp, i64, vp, i64],
+        "sbx_read_history": [vp, vp, i64, C.POINTER(i64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -196,6 +198,22 @@ def sbx_wait_selftest(ctx, polls, arrive):
 
 def sbx_set_mass(ctx, mass):
     _check(ctx, load().sbx_set_mass(ctx, _ptr(mass, np.float64)))
+
+
+def sbx_set_receivers(ctx, rec_idx, max_steps):
+    """Record U at the state-array entries rec_idx after every later step
+    (at most max_steps rows); an empty rec_idx turns recording off."""
+    idx = np.ascontiguousarray(rec_idx, np.int64)
+    _check(ctx, load().sbx_set_receivers(ctx, int(idx.size), _ptr(idx, np.int64) if idx.size else None,
+                                         int(max_steps)))
+
+
+def sbx_read_history(ctx, n_rec, max_rows):
+    """The recorded rows as an array [rows, n_rec]."""
+    out = np.empty((int(max_rows), int(n_rec)))
+    n = C.c_int64()
+    _check(ctx, load().sbx_read_history(ctx, _ptr(out, np.float64), int(max_rows), C.byref(n)))
+    return out[:n.value]
 
 
 def sbx_query(ctx, what) -> int:

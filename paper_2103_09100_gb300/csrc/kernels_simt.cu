@@ -13,6 +13,8 @@
 // a broadcast and 32 distinct displacement entries.
 #include <math.h>
 
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "sbx_internal.cuh"
 
@@ -321,6 +323,26 @@ __global__ void k_widen_f32(int64_t nn, const float4 *f, double *out) {
     out[3 * i + 1] = f2d_bits(v.y);
     out[3 * i + 2] = f2d_bits(v.z);
   }
+}
+
+// Receiver time history: row = (device step index after the update) -
+// step0 - 1, i.e. the step just taken; rows past the capacity are dropped.
+__global__ void k_record(const int64_t *__restrict__ d_step, int64_t step0, int64_t cap,
+                         int64_t n_rec, const int64_t *__restrict__ rec,
+                         const double *__restrict__ u, double *__restrict__ hist) {
+  const int64_t row = *d_step - step0 - 1;
+  if (row < 0 || row >= cap) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_rec;
+       i += (int64_t)gridDim.x * blockDim.x)
+    hist[row * n_rec + i] = u[rec[i]];
+}
+
+cudaError_t launch_record(const sbx_ctx *ctx, const double *u, cudaStream_t s) {
+  if (ctx->n_rec_hist == 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((ctx->n_rec_hist + 255) / 256, 152);
+  k_record<<<grid, 256, 0, s>>>(ctx->d_step, ctx->rec_step0, ctx->rec_cap, ctx->n_rec_hist,
+                                ctx->d_rec_idx, u, ctx->d_hist);
+  return cudaGetLastError();
 }
 
 __global__ void k_make_w(int64_t nd, const double *minv, double *w, double c) {

@@ -118,6 +118,8 @@ void free_mesh(sbx_ctx *ctx) {
   dfree(ctx->d_load_kind);
   dfree(ctx->d_tc_K); dfree(ctx->d_tc_rec); dfree(ctx->d_gen_tiles); dfree(ctx->d_gen_K);
   dfree(ctx->d_gen_koff);
+  dfree(ctx->d_rec_idx); dfree(ctx->d_hist);
+  ctx->n_rec_hist = ctx->rec_cap = 0;
   ctx->n_gen_tiles = 0;
   dfree(ctx->d_b_rec);
   for (int c = 0; c < 3; ++c) {
@@ -195,7 +197,9 @@ int one_step(sbx_ctx *ctx, int parity, double dt, double alpha, int zero_f) {
   double *uc = ctx->d_u[parity], *up = ctx->d_u[parity ^ 1];
   int rc = force(ctx, uc, ctx->d_f, dt);
   if (rc) return rc;
-  return update(ctx, uc, up, dt, alpha, zero_f);
+  if ((rc = update(ctx, uc, up, dt, alpha, zero_f))) return rc;
+  CK(sbx::launch_record(ctx, up, ctx->stream));   // up now holds U_{n+1}
+  return SBX_OK;
 }
 
 constexpr int GRAPH_UNIT = 32;  // steps per replayed graph (even)
@@ -935,6 +939,46 @@ int sbx_touch(sbx_ctx *ctx) {
   if (!ctx) return SBX_EINVAL;
   ctx->pair_valid[0] = ctx->pair_valid[1] = false;
   return SBX_OK;
+}
+
+int sbx_set_receivers(sbx_ctx *ctx, int64_t n_rec, const int64_t *rec_idx, int64_t max_steps) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
+  if (n_rec < 0 || (n_rec > 0 && (!rec_idx || max_steps < 1)))
+    return fail(ctx, SBX_EINVAL, "need n_rec >= 0, rec_idx and max_steps >= 1");
+  std::vector<int64_t> idx;
+  if (int rc = fetch_vec(ctx, idx, rec_idx, n_rec)) return rc;
+  for (int64_t q : idx)
+    if (q < 0 || q >= ctx->ndof * ctx->B) return fail(ctx, SBX_EINVAL, "receiver index out of range");
+  drop_graph(ctx);   // the step graphs hold the recording launch (or not)
+  CK(cudaStreamSynchronize(ctx->stream));
+  dfree(ctx->d_rec_idx);
+  dfree(ctx->d_hist);
+  ctx->n_rec_hist = ctx->rec_cap = 0;
+  if (n_rec == 0) return SBX_OK;
+  if (upload(ctx, &ctx->d_rec_idx, idx) || dalloc(ctx, &ctx->d_hist, n_rec * max_steps))
+    return fail(ctx, SBX_ENOMEM, "receiver history allocation failed");
+  ctx->n_rec_hist = n_rec;
+  ctx->rec_cap = max_steps;
+  ctx->rec_step0 = ctx->step;
+  return SBX_OK;
+}
+
+int sbx_read_history(sbx_ctx *ctx, double *out, int64_t max_rows, int64_t *n_rows) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!out || !n_rows || max_rows < 0) return fail(ctx, SBX_EINVAL, "bad arguments");
+  if (ctx->n_rec_hist == 0) return fail(ctx, SBX_ESTATE, "no receivers set");
+  const int64_t rows = std::min(std::min(ctx->step - ctx->rec_step0, ctx->rec_cap), max_rows);
+  *n_rows = std::max<int64_t>(rows, 0);
+  if (*n_rows > 0)
+    CK(cudaMemcpyAsync(out, ctx->d_hist, *n_rows * ctx->n_rec_hist * sizeof(double),
+                       cudaMemcpyDefault, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_flags(ctx);
 }
 
 int sbx_set_mass(sbx_ctx *ctx, const double *mass) {

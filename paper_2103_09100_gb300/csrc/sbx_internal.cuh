@@ -139,6 +139,12 @@ struct sbx_ctx {
   int n_b_tiles[3] = {}, b_nnmax[3] = {}, b_recmax[3] = {};
   size_t b_smem[3] = {};
 
+  // receiver time history (sbx_set_receivers): hist[row][n_rec], row = step
+  // index - rec_step0 - 1 of the step just taken, rows < rec_cap
+  int64_t *d_rec_idx = nullptr;
+  double *d_hist = nullptr;
+  int64_t n_rec_hist = 0, rec_cap = 0, rec_step0 = 0;
+
   // loads
   int n_load = 0;
   int64_t *d_load_dof = nullptr;
@@ -185,6 +191,9 @@ cudaError_t launch_update(const sbx_ctx *ctx, const double *uc, double *up, doub
 cudaError_t launch_init_um1(const sbx_ctx *ctx, const double *u0, const double *v0, double *um1,
                             const double *f, double dt, double alpha, cudaStream_t s);
 cudaError_t launch_zero_fixed(const sbx_ctx *ctx, double *u, cudaStream_t s);
+// receiver history: copy U at the receivers into the row of the step just
+// taken (read from the device step index)
+cudaError_t launch_record(const sbx_ctx *ctx, const double *u, cudaStream_t s);
 // Opt every kernel into the shared-memory size it may need (call once per
 // device, outside stream capture).
 cudaError_t prepare_kernels();

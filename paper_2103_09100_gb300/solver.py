@@ -79,6 +79,16 @@ class Solver:
     def step(self, n):
         L.step_n(self.ctx, n, self.dt, self.alpha)
 
+    def set_receivers(self, rec_idx, max_steps):
+        """Record U at these state-array entries after every later step."""
+        self._n_rec = int(np.size(rec_idx))
+        self._rec_cap = int(max_steps)
+        L.sbx_set_receivers(self.ctx, rec_idx, max_steps)
+
+    def history(self):
+        """[steps recorded, receivers] displacement history."""
+        return L.sbx_read_history(self.ctx, self._n_rec, self._rec_cap)
+
     def field(self, which=L.SBX_U_N, out=None):
         n = self.n_dof * (1 if which == L.SBX_MASS else self.n_rhs)
         out = np.empty(n) if out is None else out
