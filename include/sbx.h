@@ -319,6 +319,28 @@ int sbx_set_receivers(sbx_ctx *ctx, int64_t n_rec, const int64_t *rec_idx, int64
 int sbx_read_history(sbx_ctx *ctx, double *out, int64_t max_rows, int64_t *n_rows);
 
 /*
+ * sbx_lanczos: k steps of the Lanczos iteration, with full
+ * reorthogonalisation (two classical Gram-Schmidt passes per step), for the
+ * free vibration problem K x = omega^2 M x of the uploaded mesh -- the cube
+ * example of Sec. 5 computes eigenfrequencies with the same K and lumped M
+ * the explicit solver steps with.  The operator is M^-1/2 K M^-1/2 on the
+ * free DOFs (M^-1 = 0 on the fixed ones); K is applied by the FP64
+ * element-by-element force kernel of the explicit step.  Output: the
+ * tridiagonal T_k, alpha[j] on its diagonal and beta[j] below it
+ * (beta[k-1] = the norm of the last residual).  The eigenvalues of T_k
+ * (Ritz values) approximate omega^2, the extreme ones first; a multiple
+ * eigenvalue appears once.  Once the Krylov space is exhausted beta
+ * vanishes and the later coefficients are 0.
+ *   v0[3N]: start vector, host or device (fixed DOFs ignored; must not
+ *   vanish on the free DOFs).  alpha, beta: host or device, k doubles each.
+ *   Holds (k + 4) 3N doubles of device memory during the call; synchronises
+ *   the context's stream.
+ *   Errors: SBX_ESTATE (no mesh), SBX_EINVAL (k outside [1, 4096], NULL, a
+ *   batched or FP32 mesh, v0 zero on the free DOFs), SBX_ENOMEM.
+ */
+int sbx_lanczos(sbx_ctx *ctx, int64_t k, const double *v0, double *alpha, double *beta);
+
+/*
  * sbx_set_mass: replace the lumped diagonal mass M_diag[3N] (Sec. 3.3) --
  * e.g. by the sum over all parts of a node-cut partition, whose interface
  * nodes receive mass from cells on several GPUs.  Values > 0; M^-1 stays 0

@@ -110,6 +110,7 @@ class OctreeMesh:
     nu: float                   # Poisson ratio (one value per mesh)
     fixed_nodes: np.ndarray     # nodes with all three DOFs fixed
     sources: list = field(default_factory=list)   # point loads (dicts)
+    fixed_dof_list: np.ndarray = None   # further single DOFs held at zero (3 node + d)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -126,7 +127,9 @@ class OctreeMesh:
 
     def fixed_dofs(self):
         f = np.asarray(self.fixed_nodes, dtype=np.int64)
-        return np.sort(np.concatenate([3 * f, 3 * f + 1, 3 * f + 2]))
+        extra = np.zeros(0, np.int64) if self.fixed_dof_list is None else \
+            np.asarray(self.fixed_dof_list, np.int64)
+        return np.unique(np.concatenate([3 * f, 3 * f + 1, 3 * f + 2, extra]))
 
     def nodes_per_cell(self):
         return (self.slot_node >= 0).sum(1)
@@ -439,6 +442,28 @@ def tiny_refined(seed=0, lmax=2, p=0.3):
     rng = np.random.default_rng(seed)
     return make_mesh("tiny_refined_%d" % seed, (1, 1, 1), 1, lmax,
                      lambda q, c, hq: rng.random(len(c)) < p)
+
+
+def cube_roller(n=8, L=8.0, E=1000.0, refine_p=0.0, seed=0):
+    """[0, L]^3 cube of n^3 cells (n a power of two), E, nu = 0.3, rho = 1,
+    roller supports on all six faces (the normal DOF of every face node held
+    at zero), no load: the eigenfrequency benchmark of the paper's cube
+    example.  refine_p > 0 refines a seeded random share of the cells once
+    more (2:1-balanced, so hanging-node patterns appear)."""
+    lv = int(round(np.log2(n)))
+    rng = np.random.default_rng(seed)
+    lmax = lv + (1 if refine_p > 0 else 0)
+    m = make_mesh("cube_roller_%d_p%g" % (n, refine_p), (1, 1, 1), lv, lmax,
+                  lambda q, c, hq: (rng.random(len(c)) < refine_p) if q == lv else np.zeros(len(c), bool),
+                  h_root=L)
+    m.E = np.full(m.n_cells, float(E))
+    x = m.node_xyz
+    tol = 1e-9 * L
+    dofs = [3 * np.nonzero((np.abs(x[:, d]) < tol) | (np.abs(x[:, d] - L) < tol))[0] + d
+            for d in range(3)]
+    m.fixed_dof_list = np.sort(np.concatenate(dofs)).astype(np.int64)
+    m.sources = []
+    return m
 
 
 CONFIGS = {

@@ -27,7 +27,8 @@ EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patte
            "mesh_upload", "set_load", "set_initial", "step_n", "sbx_get_step", "sbx_set_step",
            "read_field", "write_field", "sbx_profile", "sbx_query", "sbx_step_static",
            "set_modulus", "sbx_adjoint", "sbx_force", "sbx_update", "sbx_field_ptr", "sbx_touch",
-           "sbx_set_mass", "sbx_wait_selftest", "sbx_set_receivers", "sbx_read_history"]
+           "sbx_set_mass", "sbx_wait_selftest", "sbx_set_receivers", "sbx_read_history",
+           "sbx_lanczos"]
 SBX_LAYOUT_F64_DOF, SBX_LAYOUT_F32_NODE4, SBX_LAYOUT_F32_DOF = 0, 1, 2
 SBX_Q_KERNELS_PER_STEP, SBX_Q_FORCE_LAUNCHES, SBX_Q_TILES, SBX_Q_BRICK_TILES = 0, 1, 2, 3
 SBX_STATIC_MAX_DOF = 4 * 1024 * 1024
@@ -78,6 +79,7 @@ def load(path: str = LIB_PATH):
         "sbx_wait_selftest": [vp, i64, i32],
         "sbx_set_receivers": [vp, i64, vp, i64],
         "sbx_read_history": [vp, vp, i64, C.POINTER(i64)],
+        "sbx_lanczos": [vp, i64, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -214,6 +216,15 @@ def sbx_read_history(ctx, n_rec, max_rows):
     n = C.c_int64()
     _check(ctx, load().sbx_read_history(ctx, _ptr(out, np.float64), int(max_rows), C.byref(n)))
     return out[:n.value]
+
+
+def sbx_lanczos(ctx, k, v0):
+    """(alpha[k], beta[k]) of k Lanczos steps of M^-1/2 K M^-1/2 from v0."""
+    v = np.ascontiguousarray(v0, np.float64)
+    alpha, beta = np.empty(int(k)), np.empty(int(k))
+    _check(ctx, load().sbx_lanczos(ctx, int(k), _ptr(v, np.float64), _ptr(alpha, np.float64),
+                                   _ptr(beta, np.float64)))
+    return alpha, beta
 
 
 def sbx_query(ctx, what) -> int:

@@ -941,6 +941,44 @@ int sbx_touch(sbx_ctx *ctx) {
   return SBX_OK;
 }
 
+int sbx_lanczos(sbx_ctx *ctx, int64_t k, const double *v0, double *alpha, double *beta) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
+  if (k < 1 || k > 4096 || !v0 || !alpha || !beta)
+    return fail(ctx, SBX_EINVAL, "need 1 <= k <= 4096 and non-NULL v0, alpha, beta");
+  if (ctx->B != 1 || ctx->prec == SBX_PREC_FP32)
+    return fail(ctx, SBX_EINVAL, "sbx_lanczos needs a single-load-case FP64 or mixed mesh");
+  std::vector<double> hv0;
+  if (int rc = fetch_vec(ctx, hv0, v0, ctx->ndof)) return rc;
+  double s2 = 0.0;
+  {
+    std::vector<char> fixed(ctx->ndof, 0);
+    for (int64_t d : ctx->h_fixed) fixed[d] = 1;
+    for (int64_t d = 0; d < ctx->ndof; ++d)
+      if (!fixed[d]) s2 += hv0[d] * hv0[d];
+  }
+  if (!(s2 > 0) || !std::isfinite(s2)) return fail(ctx, SBX_EINVAL, "v0 vanishes on the free DOFs");
+  double *dv0 = nullptr, *dab = nullptr;
+  if (upload(ctx, &dv0, hv0) || dalloc(ctx, &dab, 2 * k)) {
+    dfree(dv0);
+    return fail(ctx, SBX_ENOMEM, "Lanczos buffers");
+  }
+  CK(cudaMemsetAsync(dab, 0, 2 * k * sizeof(double), ctx->stream));
+  std::string e;
+  int rc = sbx::lanczos_run(ctx, k, dv0, dab, dab + k, e);
+  if (rc == SBX_OK &&
+      (cudaMemcpy(alpha, dab, k * sizeof(double), cudaMemcpyDefault) != cudaSuccess ||
+       cudaMemcpy(beta, dab + k, k * sizeof(double), cudaMemcpyDefault) != cudaSuccess)) {
+    rc = SBX_ECUDA;
+    e = "copy of the Lanczos coefficients failed";
+  }
+  dfree(dv0);
+  dfree(dab);
+  return rc ? fail(ctx, rc, e) : SBX_OK;
+}
+
 int sbx_set_receivers(sbx_ctx *ctx, int64_t n_rec, const int64_t *rec_idx, int64_t max_steps) {
   if (!ctx) return SBX_EINVAL;
   if (int rc = set_device(ctx)) return rc;

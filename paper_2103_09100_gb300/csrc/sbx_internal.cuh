@@ -204,6 +204,10 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
              std::string &err);
 cudaError_t prepare_tc_kernels();
 cudaError_t launch_wait_selftest(const sbx_ctx *ctx, uint32_t polls, int arrive, cudaStream_t s);
+// kernels_eigen.cu: k Lanczos steps (full reorthogonalisation) of
+// M^-1/2 K M^-1/2 from v0 (device, 3N); alpha, beta: device, k doubles
+int lanczos_run(sbx_ctx *ctx, int64_t k, const double *v0_dev, double *alpha_dev,
+                double *beta_dev, std::string &err);
 // kernels_batch.cu
 int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<int64_t> &conn_off,
                 const std::vector<int64_t> &cnt, const std::vector<uint8_t> &sym_sorted,

@@ -22,7 +22,7 @@ WAVES = {"ricker": L.SBX_WAVE_RICKER, "triangle": L.SBX_WAVE_TRIANGLE,
 class Solver:
     def __init__(self, slot_node, mask, h, E, rho, nu, n_nodes, fixed_nodes=(), sources=(),
                  precision="fp64", n_rhs=1, device=0, stream=None, dt=None, dt_factor=0.5,
-                 alpha=0.0):
+                 alpha=0.0, fixed_dofs=()):
         self.n_nodes = int(n_nodes)
         self.n_cells = int(len(mask))
         self.n_rhs = int(n_rhs)
@@ -39,7 +39,9 @@ class Solver:
         self.masters = masters
         self.pattern_counts = np.bincount(cell_pattern, minlength=len(masters))
         fixed_nodes = np.asarray(fixed_nodes, np.int64)
-        fixed = np.sort(np.concatenate([3 * fixed_nodes + d for d in range(3)])).astype(np.int64)
+        fixed = np.unique(np.concatenate([3 * fixed_nodes + d for d in range(3)] +
+                                         [np.asarray(fixed_dofs, np.int64)])).astype(np.int64)
+        self.fixed = fixed
         self.ctx = L.sbx_create(device, stream)
         try:
             L.set_patterns(self.ctx, nn, K, Ml)
@@ -55,7 +57,8 @@ class Solver:
     @classmethod
     def from_mesh(cls, mesh, **kw):
         return cls(mesh.slot_node, mesh.mask, mesh.h, mesh.E, mesh.rho, mesh.nu, mesh.n_nodes,
-                   fixed_nodes=mesh.fixed_nodes, sources=mesh.sources, **kw)
+                   fixed_nodes=mesh.fixed_nodes, sources=mesh.sources,
+                   fixed_dofs=mesh.fixed_dofs(), **kw)
 
     def set_sources(self, sources):
         kinds = {s["wavelet"] for s in sources}
