@@ -42,29 +42,38 @@ __global__ void k_mask(int64_t n, const double *__restrict__ a, const double *__
     y[i] = a[i] != 0.0 ? x[i] : 0.0;
 }
 
-__device__ __forceinline__ double block_sum(double v, double *red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-  return s;   // valid in thread 0
-}
-
-// part[b ncol + c] = this block's share of sum_i Q[c ld + i] w[i]
+// part[b ncol + c] = this block's share of sum_i Q[c ld + i] w[i]; eight
+// columns per pass over w, one barrier per eight columns
+constexpr int DOT_COLS = 8;
 __global__ void k_dots(int64_t n, const double *__restrict__ Q, int64_t ld, int ncol,
                        const double *__restrict__ w, double *__restrict__ part) {
-  __shared__ double red[EIG_THREADS / 32];
-  for (int c = 0; c < ncol; ++c) {
-    double s = 0.0;
+  __shared__ double red[EIG_THREADS / 32][DOT_COLS];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < ncol; c0 += DOT_COLS) {
+    const int nc = ncol - c0 < DOT_COLS ? ncol - c0 : DOT_COLS;
+    double s[DOT_COLS];
+#pragma unroll
+    for (int q = 0; q < DOT_COLS; ++q) s[q] = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-      s = fma(Q[c * ld + i], w[i], s);
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * ncol + c] = s;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int q = 0; q < DOT_COLS; ++q)
+        if (q < nc) s[q] = fma(Q[(int64_t)(c0 + q) * ld + i], wi, s[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < DOT_COLS; ++q)
+      for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_down_sync(0xffffffffu, s[q], o);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < DOT_COLS; ++q) red[wp][q] = s[q];
+    __syncthreads();
+    if (threadIdx.x < nc) {
+      double t = 0.0;
+      for (int v = 0; v < (int)(blockDim.x >> 5); ++v) t += red[v][threadIdx.x];
+      part[(int64_t)blockIdx.x * ncol + c0 + threadIdx.x] = t;
+    }
+    __syncthreads();
   }
 }
 
