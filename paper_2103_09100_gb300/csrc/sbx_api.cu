@@ -114,6 +114,10 @@ void free_mesh(sbx_ctx *ctx) {
   dfree(ctx->d_pair[0]); dfree(ctx->d_pair[1]);
   ctx->pair_valid[0] = ctx->pair_valid[1] = false;
   dfree(ctx->d_tiles_simt);
+  dfree(ctx->d_tiles_rest);
+  ctx->n_tiles_rest = 0;
+  ctx->wht_pat = -1;
+  ctx->wht_cells = 0;
   dfree(ctx->d_load_dof); dfree(ctx->d_load_amp); dfree(ctx->d_load_t1); dfree(ctx->d_load_ncyc);
   dfree(ctx->d_load_kind);
   dfree(ctx->d_tc_K); dfree(ctx->d_tc_rec); dfree(ctx->d_gen_tiles); dfree(ctx->d_gen_K);
@@ -464,6 +468,49 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   for (int p = 0; p < P; ++p)
     for (int64_t c0 = 0; c0 < cnt[p]; c0 += sbx::SIMT_TILE)
       tiles.push_back(Tile{p, (int32_t)std::min<int64_t>(sbx::SIMT_TILE, cnt[p] - c0), c0});
+  // FP64 force of the 8-node cells with the identity op in the Walsh basis
+  // of the corner reflections: T[(s, r), (n, r)] = (-1)^popcount(n & (s ^
+  // 2^r)) (n = corner a + 2 b + 4 c, r = component) has T T^T = 8 I and
+  // T K_p T^T / 8 block-diagonal with 3 x 3 blocks (checked here; any
+  // coupling between blocks beyond rounding keeps the dense path)
+  int wht_pat = -1;
+  sbx::WhtBlocks wht{};
+  for (int p = 0; p < P && wht_pat < 0; ++p) {
+    if (ctx->pat_nodes[p] != 8 || cnt[p] == 0) continue;
+    bool ident = true;
+    for (int64_t c = 0; c < cnt[p] && ident; ++c) ident = ssym[start[p] + c] == 0;
+    if (!ident) continue;
+    const double *Kp = &ctx->K_host[ctx->pat_koff[p]];
+    auto Tm = [](int row, int col) -> double {   // row = 3 s + r, col = 3 n + r'
+      const int s = row / 3, r = row % 3, n = col / 3, r2 = col % 3;
+      if (r != r2) return 0.0;
+      return (__builtin_popcount((unsigned)(n & (s ^ (1 << r)))) & 1) ? -1.0 : 1.0;
+    };
+    double Kh[24][24], kmax = 0.0, off = 0.0;
+    for (int i = 0; i < 24; ++i)
+      for (int j = 0; j < 24; ++j) {
+        double acc = 0.0;
+        for (int a = 0; a < 24; ++a) {
+          const double ta = Tm(i, a);
+          if (ta == 0.0) continue;
+          for (int b = 0; b < 24; ++b) {
+            const double tb = Tm(j, b);
+            if (tb != 0.0) acc += ta * Kp[a * 24 + b] * tb;
+          }
+        }
+        Kh[i][j] = acc / 8.0;
+        kmax = std::max(kmax, std::fabs(Kh[i][j]));
+        if (i / 3 != j / 3) off = std::max(off, std::fabs(Kh[i][j]));
+      }
+    if (!(off <= 1e-12 * kmax)) continue;
+    for (int sb = 0; sb < 8; ++sb)
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) wht.blk[9 * sb + 3 * r + c] = Kh[3 * sb + r][3 * sb + c];
+    wht_pat = p;
+  }
+  std::vector<Tile> rest;
+  for (const Tile &t : tiles)
+    if (t.pat != wht_pat) rest.push_back(t);
 
   free_mesh(ctx);
   int rc = SBX_OK;
@@ -476,6 +523,7 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   if (!rc) rc = upload(ctx, &ctx->d_minv, minv);
   if (!rc) rc = upload(ctx, &ctx->d_mass, mass);
   if (!rc) rc = upload(ctx, &ctx->d_tiles_simt, tiles);
+  if (!rc && !rest.empty()) rc = upload(ctx, &ctx->d_tiles_rest, rest);
   const int64_t nfield = ndof * n_rhs;
   if (!rc) rc = dalloc(ctx, &ctx->d_u[0], nfield);
   if (!rc) rc = dalloc(ctx, &ctx->d_u[1], nfield);
@@ -528,6 +576,10 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   ctx->pat_cstart = start;
   ctx->pat_ccount = cnt;
   ctx->n_tiles_simt = (int)tiles.size();
+  ctx->n_tiles_rest = (int)rest.size();
+  ctx->wht_pat = wht_pat;
+  ctx->wht_cells = wht_pat >= 0 ? cnt[wht_pat] : 0;
+  ctx->wht = wht;
   ctx->max_m = max_m;
   ctx->cur = 0;
   ctx->step = 0;

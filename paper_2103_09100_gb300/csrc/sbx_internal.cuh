@@ -18,6 +18,14 @@ struct Tile {
   int64_t cell0;
 };
 
+// The regular 8-node cell's K_p in the Walsh basis (FP64 form): the corner
+// reflections of the cube leave K_p invariant, so with the nodal values of
+// each component Walsh-transformed over the 2 x 2 x 2 corners, K_p falls
+// apart into eight 3 x 3 blocks (blk[9 s + 3 r + c], s = block).
+struct WhtBlocks {
+  double blk[72];
+};
+
 // Time function of the point loads (Sec. 5): kind, t1, peak, cycles.
 struct LoadTable {
   int n;                 // number of (dof, load) entries
@@ -115,6 +123,13 @@ struct sbx_ctx {
   int64_t step = 0;
   sbx::Tile *d_tiles_simt = nullptr;
   int n_tiles_simt = 0;
+  // FP64 force: the 8-node identity-op cells by the Walsh-basis kernel
+  // (pattern wht_pat, wht_cells of them), the rest by the dense tiles
+  int wht_pat = -1;
+  int64_t wht_cells = 0;
+  sbx::WhtBlocks wht{};
+  sbx::Tile *d_tiles_rest = nullptr;
+  int n_tiles_rest = 0;
   int max_m = 0;
 
   // mixed path (SBX_PREC_MIXED): tensor-core tiles of the 8-node cell and
