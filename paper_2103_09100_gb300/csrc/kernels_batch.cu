@@ -80,12 +80,34 @@ __device__ __forceinline__ T diff_of(const unsigned char *u, int q, int q0, int 
   }
 }
 
+// Walsh transform of 8 values in place (x[p] <- sum_n (-1)^popcount(p & n) x[n]).
+template <typename T>
+__device__ __forceinline__ void wht8_t(T *x) {
+#pragma unroll
+  for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if ((i & h) == 0) {
+        const T a = x[i], b = x[i + h];
+        x[i] = a + b;
+        x[i + h] = a - b;
+      }
+}
+
+// The regular 8-node cell's K_p as eight 3 x 3 blocks in the Walsh basis
+// of its corners (already divided by 8), in the kernel's number type.
+template <typename T>
+struct WhtB {
+  T blk[72];
+};
+
 template <typename T, int MM>
 __global__ void __launch_bounds__(BT_THREADS, 2)
     k_force_batch(const TcTile *__restrict__ tiles, int nchunks, const uint8_t *__restrict__ recs,
                   const T *__restrict__ Kp, const int64_t *__restrict__ koff,
                   const void *__restrict__ uv, void *__restrict__ fv, int B, LoadTable Ld,
-                  const int64_t *__restrict__ d_step, double dt, int nn_max, int rec_max) {
+                  const int64_t *__restrict__ d_step, double dt, int nn_max, int rec_max,
+                  int wht_pat, const WhtB<T> Kw) {
   extern __shared__ __align__(16) unsigned char smem[];
   const BSmem SL = bsmem(MM, nn_max, rec_max, sizeof(T));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -157,6 +179,34 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
           }
         }
       }
+      if (sizeof(T) == 4 && MM == 24 && op == 0 && pat == wht_pat) {   // (FP32: no spills)
+        // regular cell: f = T^T blockdiag(Kh) T d / 8 with the Walsh transform
+        // T over the corners (the translation in d drops out exactly)
+        T x[3][8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+          for (int r = 0; r < 3; ++r) x[r][k] = d[3 * k + r];
+        wht8_t(x[0]);
+        wht8_t(x[1]);
+        wht8_t(x[2]);
+        T y[3][8];
+#pragma unroll
+        for (int sb = 0; sb < 8; ++sb) {
+          const T *Bk = Kw.blk + 9 * sb;
+          const T v0 = x[0][sb ^ 1], v1 = x[1][sb ^ 2], v2 = x[2][sb ^ 4];
+          y[0][sb ^ 1] = Bk[0] * v0 + Bk[1] * v1 + Bk[2] * v2;
+          y[1][sb ^ 2] = Bk[3] * v0 + Bk[4] * v1 + Bk[5] * v2;
+          y[2][sb ^ 4] = Bk[6] * v0 + Bk[7] * v1 + Bk[8] * v2;
+        }
+        wht8_t(y[0]);
+        wht8_t(y[1]);
+        wht8_t(y[2]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+          for (int r = 0; r < 3; ++r) acc[3 * k + r] = y[r][k];
+      } else
 #pragma unroll
       for (int j = 0; j < MM; ++j) {
         if (j < m) {
@@ -377,11 +427,13 @@ static void launch_class(const sbx_ctx *ctx, int c, const T *K, const void *u, v
   const int nchunks = ctx->B / BC;
   const unsigned grid = (unsigned)ctx->n_b_tiles[c] * (unsigned)nchunks;
   const size_t sm = ctx->b_smem[c];
+  WhtB<T> kw;
+  for (int q = 0; q < 72; ++q) kw.blk[q] = (T)(ctx->wht.blk[q] * 0.125);
 #define SBX_LAUNCH(MMV)                                                                        \
   k_force_batch<T, MMV><<<grid, BT_THREADS, sm, s>>>(ctx->d_b_tiles[c], nchunks, ctx->d_b_rec, \
                                                      K, ctx->d_koff, u, f, ctx->B, L,          \
                                                      ctx->d_step, dt, ctx->b_nnmax[c],         \
-                                                     ctx->b_recmax[c])
+                                                     ctx->b_recmax[c], ctx->wht_pat, kw)
   if (c == 0) SBX_LAUNCH(24);
   else if (c == 1) SBX_LAUNCH(48);
   else SBX_LAUNCH(80);
