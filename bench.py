@@ -3,9 +3,11 @@
 One step = the whole hot path: gather, K_p contraction, scatter, source
 term, lumped-mass central-difference update.  Three forms are measured:
 
-* headline (``value``): the mixed-precision form (TF32x3 tensor-core
-  contraction, FP64 history) on the cube-with-spherical-cavity octree
-  (levels 4-8, ~1.02M cells, ~3.44M DOF, lognormal E_e, Ricker load);
+* headline (``value``): the mixed-precision form (FP32 differences to slot 0,
+  the regular cells' K_p applied in the Walsh basis of their corners -- or
+  TF32x3 on the tensor cores, sbx_set_mixed_kernel -- FP64 history) on the
+  cube-with-spherical-cavity octree (levels 4-8, ~1.02M cells, ~3.44M DOF,
+  lognormal E_e, Ricker load);
 * ``forms.fp64``: the plain FP64 form on the same mesh;
 * ``forms.batched``: 64 load cases per launch (FP32 contraction, FP64
   history) on the multi-point octree (levels 3-7, ~200k cells); its unit is
@@ -46,10 +48,14 @@ UNIT = "DOF*steps/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA pipe of GB300: 2 DFMA / clk / SM x 152 SMs x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TOPS = 2 * 152 * 2.07e9 / 1e12   # FP64 pipe operations per second (T)
 # DRAM bytes (read + write) of one force launch pair on the cavity cube, from
-# the ncu capture summarised in profiles/k_force_tc_mixed_cavity_cube.md
-# (k_force_tc 67.6 MB + k_force_gen 13.1 MB); valid for that kernel version
-FORCE_TRAFFIC_MIXED = 80.7e6
+# the ncu captures summarised in profiles/: the tensor-core kernel's pair
+# (k_force_tc 67.6 MB + k_force_gen 13.1 MB, k_force_tc_mixed_cavity_cube.md)
+# and the Walsh kernel's pair (None until captured); valid for those
+# kernel versions
+FORCE_TRAFFIC_MIXED_TC = 80.7e6
+FORCE_TRAFFIC_MIXED_WALSH = None
 
 
 def dist_env():
@@ -79,6 +85,20 @@ def algorithmic_bytes(mesh, nper, B=1):
 def contraction_flops(nper, B=1):
     m = 3 * nper.astype(np.float64)
     return float(np.sum(2 * m * m)) * B
+
+
+# FP64 pipe operations (DFMA, DADD, DMUL: one each) of one force evaluation:
+# a regular cell in the Walsh basis takes 3 x (24 + 24) butterfly add/sub,
+# 8 x 9 block operations and 24 scalings; any other cell m_p^2 DFMA
+WALSH_OPS_PER_CELL = 3 * 48 + 72 + 24
+
+
+def fp64_ops(nper, walsh_cells):
+    m = 3 * nper.astype(np.float64)
+    dense = float(np.sum(m * m))
+    if walsh_cells:
+        dense -= walsh_cells * 24.0 * 24.0
+    return dense + walsh_cells * WALSH_OPS_PER_CELL
 
 
 class ClockSampler:
@@ -267,21 +287,28 @@ def main():
     t_update = ms_u / prof_steps * 1e-3
     flops = contraction_flops(nper)
     bytes_step, bytes_force = algorithmic_bytes(mesh, nper)
+    walsh_cells = L.sbx_query(S.ctx, L.SBX_Q_WALSH_CELLS)
     if args.precision == "fp64":
-        ach = flops / t_force / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "k_force_simt<double> (DFMA contraction)",
-                "peak_source": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)"}
+        ach = fp64_ops(nper, walsh_cells) / t_force / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TOPS,
+                "unit": "T FP64 ops/s (DFMA, DADD, DMUL one each)",
+                "frac": ach / FP64_PEAK_TOPS, "traffic": None,
+                "kernel": "k_force_wht (8-node cells, Walsh basis) + k_force_simt<double> "
+                          "(other patterns)" if walsh_cells else "k_force_simt<double>",
+                "peak_source": "FP64 pipe: 2 ops/clk/SM x 152 SMs x 2.07 GHz (derived)",
+                "dense_equivalent_tflops": flops / t_force / 1e12}
     else:
         ach = bytes_force / t_force / 1e9
         mixed = args.precision == "mixed"
         roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"],
-                "traffic": FORCE_TRAFFIC_MIXED if mixed else None,
-                "kernel": "force launch pair k_force_tc + k_force_gen (concurrent streams)"
+                "traffic": (FORCE_TRAFFIC_MIXED_WALSH if walsh_cells else FORCE_TRAFFIC_MIXED_TC)
+                if mixed else None,
+                "kernel": ("force launch pair k_force_wht32 (8-node cells, Walsh basis) + "
+                           "k_force_gen (concurrent streams)" if walsh_cells else
+                           "force launch pair k_force_tc (tcgen05) + k_force_gen (concurrent streams)")
                 if mixed else "k_force_simt<float>", "peak_source": "hbm_gbs " + pk_src}
-        if args.precision == "mixed":
+        if mixed and not walsh_cells:
             roof["tensor_tflops_tf32"] = 3 * flops / t_force / 1e12
     roof.update({"algorithmic_bytes_per_launch": bytes_force, "force_ms": t_force * 1e3,
                  "update_ms": t_update * 1e3,
@@ -314,7 +341,9 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": {"fp64": "f64", "fp32": "f32 contraction, f64 state",
-                     "mixed": "tf32x3 contraction (f32 accumulate), f64 state"}[args.precision],
+                     "mixed": ("f32 contraction (8-node cells in the Walsh basis), f64 state"
+                               if walsh_cells else
+                               "tf32x3 contraction (f32 accumulate), f64 state")}[args.precision],
            "data": "synthetic",
            "config": {"workload": mesh.name + " (cube minus r=0.2 ball, levels 4-8, lognormal E)",
                       "cells": mesh.n_cells, "dof": mesh.n_dof, "patterns": len(S.masters),

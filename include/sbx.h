@@ -341,6 +341,21 @@ int sbx_read_history(sbx_ctx *ctx, double *out, int64_t max_rows, int64_t *n_row
 int sbx_lanczos(sbx_ctx *ctx, int64_t k, const double *v0, double *alpha, double *beta);
 
 /*
+ * sbx_set_mixed_kernel: mixed form (one load case) only -- which kernel
+ * applies K_p to the regular 8-node cells (the other patterns always run
+ * on the FP32 SIMT pattern kernel): SBX_MIXED_TENSOR (TF32x3 on the tensor
+ * cores, tcgen05, accumulators in tensor memory) or SBX_MIXED_WALSH (FP32
+ * SIMT in the Walsh basis of the cell's corners, where K_p is eight 3 x 3
+ * blocks).  Both take the same tiles, differences to slot 0 and node sums;
+ * the Walsh kernel is available (and the default) when the 8-node
+ * pattern's K_p passed the block check at mesh_upload.
+ *   Errors: SBX_EINVAL (ctx NULL, unknown kind, Walsh not available).
+ */
+#define SBX_MIXED_TENSOR 0
+#define SBX_MIXED_WALSH  1
+int sbx_set_mixed_kernel(sbx_ctx *ctx, int kind);
+
+/*
  * sbx_set_mass: replace the lumped diagonal mass M_diag[3N] (Sec. 3.3) --
  * e.g. by the sum over all parts of a node-cut partition, whose interface
  * nodes receive mass from cells on several GPUs.  Values > 0; M^-1 stays 0
@@ -356,12 +371,16 @@ int sbx_set_mass(sbx_ctx *ctx, const double *mass);
  *          SBX_Q_TILES             CTAs of all force launches of one step
  *          SBX_Q_BRICK_TILES       mixed form: tensor-core tiles that are
  *                                  complete 4 x 4 x 8 blocks of 8-node cells
+ *          SBX_Q_WALSH_CELLS       cells whose K_p is applied in the Walsh
+ *                                  basis of their corners (FP64 form, batched
+ *                                  FP32 form, mixed form on SBX_MIXED_WALSH)
  *   Errors: SBX_ESTATE (no mesh), SBX_EINVAL (unknown item, NULL out).
  */
 #define SBX_Q_KERNELS_PER_STEP 0
 #define SBX_Q_FORCE_LAUNCHES   1
 #define SBX_Q_TILES            2
 #define SBX_Q_BRICK_TILES      3
+#define SBX_Q_WALSH_CELLS      5
 int sbx_query(sbx_ctx *ctx, int what, int64_t *out);
 
 /*

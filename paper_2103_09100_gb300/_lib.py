@@ -28,9 +28,11 @@ EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patte
            "read_field", "write_field", "sbx_profile", "sbx_query", "sbx_step_static",
            "set_modulus", "sbx_adjoint", "sbx_force", "sbx_update", "sbx_field_ptr", "sbx_touch",
            "sbx_set_mass", "sbx_wait_selftest", "sbx_set_receivers", "sbx_read_history",
-           "sbx_lanczos"]
+           "sbx_lanczos", "sbx_set_mixed_kernel"]
 SBX_LAYOUT_F64_DOF, SBX_LAYOUT_F32_NODE4, SBX_LAYOUT_F32_DOF = 0, 1, 2
 SBX_Q_KERNELS_PER_STEP, SBX_Q_FORCE_LAUNCHES, SBX_Q_TILES, SBX_Q_BRICK_TILES = 0, 1, 2, 3
+SBX_MIXED_TENSOR, SBX_MIXED_WALSH = 0, 1
+SBX_Q_WALSH_CELLS = 5
 SBX_STATIC_MAX_DOF = 4 * 1024 * 1024
 SBX_STATIC_MAX_PATTERNS = 144
 
@@ -80,6 +82,7 @@ def load(path: str = LIB_PATH):
         "sbx_set_receivers": [vp, i64, vp, i64],
         "sbx_read_history": [vp, vp, i64, C.POINTER(i64)],
         "sbx_lanczos": [vp, i64, vp, vp, vp],
+        "sbx_set_mixed_kernel": [vp, i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -225,6 +228,10 @@ def sbx_lanczos(ctx, k, v0):
     _check(ctx, load().sbx_lanczos(ctx, int(k), _ptr(v, np.float64), _ptr(alpha, np.float64),
                                    _ptr(beta, np.float64)))
     return alpha, beta
+
+
+def sbx_set_mixed_kernel(ctx, kind):
+    _check(ctx, load().sbx_set_mixed_kernel(ctx, int(kind)))
 
 
 def sbx_query(ctx, what) -> int:

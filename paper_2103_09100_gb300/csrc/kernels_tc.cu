@@ -157,6 +157,45 @@ __device__ __forceinline__ void node_diff(const float *p, const float *r, float 
   d2 = (b.x - rb.x) + (c.y - rc.y);
 }
 
+// Brick tiles: node sums of one corner layer by warp shuffles.  v[3 t + r]
+// holds component r of corner (t & 1, t >> 1, h) of this lane's cell, already
+// scaled by E h; lane = x + 4 y + 16 zl, cell (x, y, z = 2 (w % 4) + zl).
+// The node (a, b) of lattice layer z + h sums corner (dx, dy) of the cells
+// (a - dx, b - dy): lane (x, y) forms node (x, y) (and (4, y), (x, 4),
+// (4, 4) on the +x / +y rows) from its own corners and its -x, -y, -x-y
+// neighbours' (warp shuffles), one vector reduction per node.
+__device__ __forceinline__ void brick_node_sums(const Stage &S, const float *v, int warp,
+                                                int lane, int h, float *f4) {
+  const int x = lane & 3, y = (lane >> 2) & 3;
+  float s1[6], s4[6], s5[3];   // from lane - 1: corners 1, 3; lane - 4: 2, 3; lane - 5: 3
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    s1[r] = __shfl_up_sync(0xffffffffu, v[3 + r], 1);
+    s1[3 + r] = __shfl_up_sync(0xffffffffu, v[9 + r], 1);
+    s4[r] = __shfl_up_sync(0xffffffffu, v[6 + r], 4);
+    s4[3 + r] = __shfl_up_sync(0xffffffffu, v[9 + r], 4);
+    s5[r] = __shfl_up_sync(0xffffffffu, v[9 + r], 5);
+  }
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {   // neighbours outside the layer contribute nothing
+    s1[r] = x > 0 ? s1[r] : 0.0f;
+    s4[r] = y > 0 ? s4[r] : 0.0f;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) s5[r] = (x > 0 && y > 0) ? s5[r] : 0.0f;
+  const int base = 25 * (2 * (warp & 3) + ((lane >> 4) & 1) + h);
+  red_add_v4(f4 + 4 * (int64_t)S.nodes[base + x + 5 * y], v[0] + s1[0] + s4[0] + s5[0],
+             v[1] + s1[1] + s4[1] + s5[1], v[2] + s1[2] + s4[2] + s5[2]);
+  if (x == 3)   // node (4, y): own corner (1, 0), cell (3, y - 1) corner (1, 1)
+    red_add_v4(f4 + 4 * (int64_t)S.nodes[base + 4 + 5 * y], v[3] + s4[3], v[4] + s4[4],
+               v[5] + s4[5]);
+  if (y == 3)   // node (x, 4): own corner (0, 1), cell (x - 1, 3) corner (1, 1)
+    red_add_v4(f4 + 4 * (int64_t)S.nodes[base + x + 20], v[6] + s1[3], v[7] + s1[4],
+               v[8] + s1[5]);
+  if (x == 3 && y == 3)   // node (4, 4)
+    red_add_v4(f4 + 4 * (int64_t)S.nodes[base + 24], v[9], v[10], v[11]);
+}
+
 // external load of the step (Sec. 5), added into the FP32 accumulator
 __device__ __forceinline__ void add_loads(const LoadTable &Ld, const int64_t *d_step, double dt,
                                           float *f4) {
@@ -356,42 +395,10 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
       }
       tc::fence_before_sync();
       if (brick) {
-        // lane = x + 4 y + 16 zl holds corners (dx, dy, dz = h) of cell
-        // (x, y, z = 2 (w % 4) + zl); the node (a, b) of lattice layer z + h
-        // sums corner (dx, dy) of the cells (a - dx, b - dy): lane (x, y) forms
-        // node (x, y) (and (4, y), (x, 4), (4, 4) on the +x / +y rows) from
-        // its own corners and its -x, -y, -x-y neighbours' (warp shuffles)
-        const int lane = tid & 31, x = lane & 3, y = (lane >> 2) & 3;
         const float sc = S.scale[fc];
 #pragma unroll
         for (int q = 0; q < 12; ++q) v[q] *= sc;
-        float s1[6], s4[6], s5[3];   // from lane - 1: corners 1, 3; lane - 4: 2, 3; lane - 5: 3
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          s1[r] = __shfl_up_sync(0xffffffffu, v[3 + r], 1);
-          s1[3 + r] = __shfl_up_sync(0xffffffffu, v[9 + r], 1);
-          s4[r] = __shfl_up_sync(0xffffffffu, v[6 + r], 4);
-          s4[3 + r] = __shfl_up_sync(0xffffffffu, v[9 + r], 4);
-          s5[r] = __shfl_up_sync(0xffffffffu, v[9 + r], 5);
-        }
-#pragma unroll
-        for (int r = 0; r < 6; ++r) {   // neighbours outside the layer contribute nothing
-          s1[r] = x > 0 ? s1[r] : 0.0f;
-          s4[r] = y > 0 ? s4[r] : 0.0f;
-        }
-#pragma unroll
-        for (int r = 0; r < 3; ++r) s5[r] = (x > 0 && y > 0) ? s5[r] : 0.0f;
-        const int base = 25 * (2 * (warp & 3) + ((lane >> 4) & 1) + fh);
-        red_add_v4(f4 + 4 * (int64_t)S.nodes[base + x + 5 * y], v[0] + s1[0] + s4[0] + s5[0],
-                   v[1] + s1[1] + s4[1] + s5[1], v[2] + s1[2] + s4[2] + s5[2]);
-        if (x == 3)   // node (4, y): own corner (1, 0), cell (3, y - 1) corner (1, 1)
-          red_add_v4(f4 + 4 * (int64_t)S.nodes[base + 4 + 5 * y], v[3] + s4[3], v[4] + s4[4],
-                     v[5] + s4[5]);
-        if (y == 3)   // node (x, 4): own corner (0, 1), cell (x - 1, 3) corner (1, 1)
-          red_add_v4(f4 + 4 * (int64_t)S.nodes[base + x + 20], v[6] + s1[3], v[7] + s1[4],
-                     v[8] + s1[5]);
-        if (x == 3 && y == 3)   // node (4, 4)
-          red_add_v4(f4 + 4 * (int64_t)S.nodes[base + 24], v[9], v[10], v[11]);
+        brick_node_sums(S, v, warp, tid & 31, fh, f4);
       } else if (fc < ncell) {
         const float sc = S.scale[fc];
 #pragma unroll
@@ -431,6 +438,211 @@ __global__ void __launch_bounds__(TC_THREADS, 4)
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(taddr, (uint32_t)TCOLS);
+}
+
+// ------------------------------------------------- Walsh-basis SIMT variant
+// The same tiles, records and node sums as k_force_tc, one thread per cell
+// (128 threads per tile) and no tensor cores: the regular cell's K_p is
+// block-diagonal in the Walsh basis of its corners (eight 3 x 3 blocks;
+// see mesh_upload), so the differences to slot 0 are Walsh-transformed per
+// component, multiplied block by block and transformed back in FP32
+// registers (~300 operations per cell against a 24 x 24 contraction).
+constexpr int WT_THREADS = 128;
+
+struct WhtF {
+  float blk[72];   // blocks of T K_p T^T / 8, divided by 8 once more (T T^T = 8 I)
+};
+
+struct WtLayout {
+  uint32_t F, stage[2], u_off, total;
+};
+__host__ __device__ inline WtLayout wt_layout(int rec_max, int nn_max) {
+  WtLayout L;
+  uint32_t o = 128;   // 2 record mbarriers
+  L.F = o;   o = a128(o + 8u * 128u * 16u);
+  L.u_off = a16((uint32_t)rec_max);
+  const uint32_t st = a128(L.u_off + 24u * (uint32_t)nn_max);
+  L.stage[0] = o; o += st;
+  L.stage[1] = o; o += st;
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ void wht8f(float *x) {
+#pragma unroll
+  for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if ((i & h) == 0) {
+        const float a = x[i], b = x[i + h];
+        x[i] = a + b;
+        x[i + h] = a - b;
+      }
+}
+
+__global__ void __launch_bounds__(WT_THREADS, 4)
+    k_force_wht32(const TcTile *__restrict__ tiles, int ntiles, const uint8_t *__restrict__ recs,
+                  const WhtF Kw, const float *__restrict__ u, float *__restrict__ f4, LoadTable Ld,
+                  const int64_t *__restrict__ d_step, double dt, int32_t *flags, int rec_max,
+                  int nn_max) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const WtLayout SL = wt_layout(rec_max, nn_max);
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [0], [1] records of stage 0, 1
+  float4 *F4 = reinterpret_cast<float4 *>(smem + SL.F);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x;
+  const uint32_t mb_rec0 = tc::smem_addr(&mbar[0]);
+  if (tid == 0) {
+    tc::mbar_init(mb_rec0, 1);
+    tc::mbar_init(mb_rec0 + 8u, 1);
+    tc::mbar_fence_init();
+  }
+  if (blockIdx.x == 0 && Ld.n > 0) add_loads(Ld, d_step, dt, f4);
+  __syncthreads();
+
+  auto stage_base = [&](int s) { return smem + (s ? SL.stage[1] : SL.stage[0]); };
+  auto issue_record = [&](int s, const TcTile &T) {   // thread 0 only
+    tc::fence_proxy_async_smem();
+    const uint32_t mb = mb_rec0 + 8u * (uint32_t)s;
+    tc::mbar_arrive_expect_tx(mb, (uint32_t)T.rec_bytes);
+    tc::bulk_g2s(tc::smem_addr(stage_base(s)), recs + T.rec_off, (uint32_t)T.rec_bytes, mb);
+  };
+  auto issue_gather = [&](int s) {            // all threads
+    const Stage S = stage_view(stage_base(s), SL.u_off);
+    const int nn = S.hdr[2];
+    const uint32_t ub = tc::smem_addr(S.u);
+    for (int i = tid; i < nn; i += WT_THREADS) {
+      const float *src = u + 6 * (int64_t)S.nodes[i];
+      tc::cp_async8(ub + 24u * i, src);
+      tc::cp_async8(ub + 24u * i + 8u, src + 2);
+      tc::cp_async8(ub + 24u * i + 16u, src + 4);
+    }
+    tc::cp_async_commit();
+  };
+
+  uint32_t ph_rec = 0u, pend = 0u;
+  bool ok = true;
+  int tile = blockIdx.x;
+  if (tile < ntiles) {
+    if (tid == 0) {
+      issue_record(0, tiles[tile]);
+      if (tile + G < ntiles) issue_record(1, tiles[tile + G]);
+    }
+    pend = 1u | (tile + G < ntiles ? 2u : 0u);
+    ok = __syncthreads_and(tc::mbar_wait_bounded(mb_rec0, ph_rec & 1u, WAIT_POLLS));
+    if (ok) {
+      ph_rec ^= 1u;
+      pend &= ~1u;
+      issue_gather(0);
+    }
+  }
+  const int fc = tid;   // this thread's cell
+  TcTile ahead;         // descriptor of the tile after next (thread 0), fetched a tile early
+  for (int i = 0; ok && tile < ntiles; ++i, tile += G) {
+    const int s = i & 1;
+    const uint32_t so = (uint32_t)(s ^ 1);
+    const int next = tile + G;
+    tc::cp_async_wait_all();
+    __syncthreads();
+    if (i > 0 && next < ntiles) {   // every thread is past the previous tile: its stage is free
+      if (tid == 0) issue_record((int)so, ahead);
+      pend |= 1u << so;
+    }
+    if (tid == 0 && next + G < ntiles) ahead = tiles[next + G];
+    const Stage S = stage_view(stage_base(s), SL.u_off);
+    const int ncell = S.hdr[1], nn = S.hdr[2];
+    const bool brick = S.hdr[3] == 1;
+    // o[r][k]: component r at corner k = a + 2 b + 4 c of this cell's force
+    float o[3][8];
+    if (fc < ncell) {
+      uint32_t lk[8];
+      if (brick) {   // lattice node index a + 5 b + 25 c
+        const int b0 = (fc & 3) + 5 * ((fc >> 2) & 3) + 25 * (fc >> 4);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) lk[k] = (uint32_t)(b0 + (k & 1) + 5 * ((k >> 1) & 1) + 25 * (k >> 2));
+      } else {
+        const uint4 Lw = *reinterpret_cast<const uint4 *>(S.lid + 8 * fc);
+        const uint32_t w4[4] = {Lw.x, Lw.y, Lw.z, Lw.w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) lk[k] = (w4[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
+      }
+      const float *ref = S.u + 6 * lk[0];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) node_diff(S.u + 6 * lk[k], ref, o[0][k], o[1][k], o[2][k]);
+      wht8f(o[0]);
+      wht8f(o[1]);
+      wht8f(o[2]);
+      float y[3][8];
+#pragma unroll
+      for (int sb = 0; sb < 8; ++sb) {
+        const float *B = Kw.blk + 9 * sb;
+        const float v0 = o[0][sb ^ 1], v1 = o[1][sb ^ 2], v2 = o[2][sb ^ 4];
+        y[0][sb ^ 1] = fmaf(B[0], v0, fmaf(B[1], v1, B[2] * v2));
+        y[1][sb ^ 2] = fmaf(B[3], v0, fmaf(B[4], v1, B[5] * v2));
+        y[2][sb ^ 4] = fmaf(B[6], v0, fmaf(B[7], v1, B[8] * v2));
+      }
+      wht8f(y[0]);
+      wht8f(y[1]);
+      wht8f(y[2]);
+      const float sc = S.scale[fc];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) o[r][k] = sc * y[r][k];
+    }
+    // the next tile's record (issued a tile ago) and the gather of its node
+    // pairs, under this tile's node sums
+    bool got = true;
+    if (next < ntiles) {
+      got = tc::mbar_wait_bounded(mb_rec0 + 8u * so, (ph_rec >> so) & 1u, WAIT_POLLS);
+      if (got) issue_gather((int)so);
+    }
+    ok = __syncthreads_and(got);
+    if (!ok) break;
+    if (next < ntiles) {
+      ph_rec ^= 1u << so;
+      pend &= ~(1u << so);
+    }
+    if (brick) {
+      if (fc < ncell) {   // (whole warps: a brick has 128 cells)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v[12];
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) v[3 * t + r] = o[r][4 * h + t];
+          brick_node_sums(S, v, warp, lane, h, f4);
+        }
+      }
+    } else {
+      if (fc < ncell)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) F4[k * 128 + fc] = make_float4(o[0][k], o[1][k], o[2][k], 0.0f);
+      __syncthreads();
+      for (int q = tid; q < nn; q += WT_THREADS) {
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+        const int j0 = S.off[q], nj = S.off[q + 1] - j0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (j < nj) {
+            const int e = S.inc[j0 + j];
+            const float4 w = F4[((e & 31) << 7) | (e >> 5)];
+            a0 += w.x;
+            a1 += w.y;
+            a2 += w.z;
+          }
+        }
+        red_add_v4(f4 + 4 * (int64_t)S.nodes[q], a0, a1, a2);
+      }
+    }
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(flags, 2);
+    tc::cp_async_wait_all();
+    if (pend & 1u) tc::mbar_wait_bounded(mb_rec0, ph_rec & 1u, WAIT_POLLS);
+    if (pend & 2u) tc::mbar_wait_bounded(mb_rec0 + 8u, (ph_rec >> 1) & 1u, WAIT_POLLS);
+  }
 }
 
 // Cells of the other patterns: one tile (<= 32 cells of pattern p) per CTA.
@@ -844,6 +1056,12 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   int per_sm = (int)((228u * 1024u) / (ctx->tc_smem[0] + 1024u));
   per_sm = std::max(1, std::min(per_sm, gen.empty() ? 4 : 3));
   ctx->tc_grid[0] = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)nsm * per_sm));
+  // Walsh-basis variant: 128 threads, no tensor memory; at most 4 CTAs per
+  // SM (its launch bounds), 3 beside k_force_gen
+  ctx->wt_smem = wt_layout(recmax, nnmax).total;
+  int per_sm_w = (int)((228u * 1024u) / (ctx->wt_smem + 1024u));
+  per_sm_w = std::max(1, std::min(per_sm_w, gen.empty() ? 4 : 3));
+  ctx->wt_grid = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)nsm * per_sm_w));
   if (ctx->tc_smem[0] > 227u * 1024u) {
     err = "tensor-core tile needs more than 227 KB of shared memory";
     return SBX_EINVAL;
@@ -867,6 +1085,8 @@ cudaError_t prepare_tc_kernels() {
   e = cudaFuncSetAttribute(k_force_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_force_wht32, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_force_gen, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)gen_smem(78));
 }
@@ -883,7 +1103,15 @@ cudaError_t launch_force_tc(const sbx_ctx *ctx, const float *pairs, float *f4, d
     if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0)) != cudaSuccess) return e;
   }
-  if (ctx->n_tc_tiles[0] > 0) {
+  if (ctx->n_tc_tiles[0] > 0 && ctx->mixed_wht && ctx->wht_pat >= 0) {
+    WhtF kw;
+    for (int q = 0; q < 72; ++q) kw.blk[q] = (float)(ctx->wht.blk[q] * 0.125);
+    k_force_wht32<<<ctx->wt_grid, WT_THREADS, ctx->wt_smem, s>>>(
+        ctx->d_tc_tiles[0], ctx->n_tc_tiles[0], ctx->d_tc_rec, kw, pairs, f4, L, ctx->d_step, dt,
+        ctx->d_flags, ctx->tc_rec_max[0], ctx->tc_nn_max[0]);
+    L.n = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if (ctx->n_tc_tiles[0] > 0) {
     k_force_tc<<<ctx->tc_grid[0], TC_THREADS, ctx->tc_smem[0], s>>>(
         ctx->d_tc_tiles[0], ctx->n_tc_tiles[0], ctx->d_tc_rec, ctx->d_tc_K, pairs, f4, L,
         ctx->d_step, dt, ctx->d_flags, ctx->tc_rec_max[0], ctx->tc_nn_max[0]);

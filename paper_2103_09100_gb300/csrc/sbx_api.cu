@@ -580,6 +580,9 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   ctx->wht_pat = wht_pat;
   ctx->wht_cells = wht_pat >= 0 ? cnt[wht_pat] : 0;
   ctx->wht = wht;
+  // mixed form: the Walsh-basis kernel for the regular cells by default
+  // (faster and more accurate than the tensor-core one on these cells)
+  ctx->mixed_wht = precision_mode == SBX_PREC_MIXED && n_rhs == 1 && wht_pat >= 0;
   ctx->max_m = max_m;
   ctx->cur = 0;
   ctx->step = 0;
@@ -1031,6 +1034,18 @@ int sbx_lanczos(sbx_ctx *ctx, int64_t k, const double *v0, double *alpha, double
   return rc ? fail(ctx, rc, e) : SBX_OK;
 }
 
+int sbx_set_mixed_kernel(sbx_ctx *ctx, int kind) {
+  if (!ctx) return SBX_EINVAL;
+  if (kind != SBX_MIXED_TENSOR && kind != SBX_MIXED_WALSH)
+    return fail(ctx, SBX_EINVAL, "unknown mixed kernel");
+  if (kind == SBX_MIXED_WALSH && ctx->wht_pat < 0)
+    return fail(ctx, SBX_EINVAL, "no Walsh blocks for this mesh");
+  const bool w = kind == SBX_MIXED_WALSH;
+  if (ctx->mixed_wht != w) drop_graph(ctx);
+  ctx->mixed_wht = w;
+  return SBX_OK;
+}
+
 int sbx_set_receivers(sbx_ctx *ctx, int64_t n_rec, const int64_t *rec_idx, int64_t max_steps) {
   if (!ctx) return SBX_EINVAL;
   if (int rc = set_device(ctx)) return rc;
@@ -1114,6 +1129,11 @@ int sbx_query(sbx_ctx *ctx, int what, int64_t *out) {
     case SBX_Q_FORCE_LAUNCHES: *out = launches; break;
     case SBX_Q_TILES: *out = tiles; break;
     case SBX_Q_BRICK_TILES: *out = (ctx->prec == SBX_PREC_MIXED && ctx->B == 1) ? ctx->n_brick_tiles : 0; break;
+    case SBX_Q_WALSH_CELLS:
+      *out = ctx->B > 1 ? (ctx->prec == SBX_PREC_FP32 ? ctx->wht_cells : 0)
+             : ctx->prec == SBX_PREC_FP64 ? ctx->wht_cells
+             : (ctx->prec == SBX_PREC_MIXED && ctx->mixed_wht) ? ctx->wht_cells : 0;
+      break;
     default: return fail(ctx, SBX_EINVAL, "unknown query");
   }
   return SBX_OK;

@@ -147,6 +147,11 @@ struct sbx_ctx {
   int64_t *d_gen_koff = nullptr;
   int n_gen_tiles = 0;
   size_t gen_smem = 0;
+  // the 8-node tiles by the Walsh-basis SIMT kernel instead of the tensor
+  // cores (sbx_set_mixed_kernel)
+  bool mixed_wht = false;
+  size_t wt_smem = 0;
+  int wt_grid = 0;
 
   // batched path (n_rhs > 1): tile records in three classes by pattern size
   uint8_t *d_b_rec = nullptr;
