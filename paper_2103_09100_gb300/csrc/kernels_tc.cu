@@ -454,12 +454,11 @@ struct WhtF {
 };
 
 struct WtLayout {
-  uint32_t F, stage[2], u_off, total;
+  uint32_t stage[2], u_off, total;
 };
 __host__ __device__ inline WtLayout wt_layout(int rec_max, int nn_max) {
   WtLayout L;
   uint32_t o = 128;   // 2 record mbarriers
-  L.F = o;   o = a128(o + 8u * 128u * 16u);
   L.u_off = a16((uint32_t)rec_max);
   const uint32_t st = a128(L.u_off + 24u * (uint32_t)nn_max);
   L.stage[0] = o; o += st;
@@ -480,7 +479,7 @@ __device__ __forceinline__ void wht8f(float *x) {
       }
 }
 
-__global__ void __launch_bounds__(WT_THREADS, 4)
+__global__ void __launch_bounds__(WT_THREADS, 5)
     k_force_wht32(const TcTile *__restrict__ tiles, int ntiles, const uint8_t *__restrict__ recs,
                   const WhtF Kw, const float *__restrict__ u, float *__restrict__ f4, LoadTable Ld,
                   const int64_t *__restrict__ d_step, double dt, int32_t *flags, int rec_max,
@@ -488,7 +487,6 @@ __global__ void __launch_bounds__(WT_THREADS, 4)
   extern __shared__ __align__(128) unsigned char smem[];
   const WtLayout SL = wt_layout(rec_max, nn_max);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [0], [1] records of stage 0, 1
-  float4 *F4 = reinterpret_cast<float4 *>(smem + SL.F);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x;
   const uint32_t mb_rec0 = tc::smem_addr(&mbar[0]);
@@ -615,25 +613,13 @@ __global__ void __launch_bounds__(WT_THREADS, 4)
           brick_node_sums(S, v, warp, lane, h, f4);
         }
       }
-    } else {
-      if (fc < ncell)
+    } else if (fc < ncell) {   // list tile: one vector reduction per corner
+      const uint4 Lw = *reinterpret_cast<const uint4 *>(S.lid + 8 * fc);
+      const uint32_t w4[4] = {Lw.x, Lw.y, Lw.z, Lw.w};
 #pragma unroll
-        for (int k = 0; k < 8; ++k) F4[k * 128 + fc] = make_float4(o[0][k], o[1][k], o[2][k], 0.0f);
-      __syncthreads();
-      for (int q = tid; q < nn; q += WT_THREADS) {
-        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
-        const int j0 = S.off[q], nj = S.off[q + 1] - j0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          if (j < nj) {
-            const int e = S.inc[j0 + j];
-            const float4 w = F4[((e & 31) << 7) | (e >> 5)];
-            a0 += w.x;
-            a1 += w.y;
-            a2 += w.z;
-          }
-        }
-        red_add_v4(f4 + 4 * (int64_t)S.nodes[q], a0, a1, a2);
+      for (int k = 0; k < 8; ++k) {
+        const int lk = (int)((w4[k >> 1] >> (16 * (k & 1))) & 0xFFFFu);
+        red_add_v4(f4 + 4 * (int64_t)S.nodes[lk], o[0][k], o[1][k], o[2][k]);
       }
     }
   }
@@ -1056,11 +1042,13 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   int per_sm = (int)((228u * 1024u) / (ctx->tc_smem[0] + 1024u));
   per_sm = std::max(1, std::min(per_sm, gen.empty() ? 4 : 3));
   ctx->tc_grid[0] = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)nsm * per_sm));
-  // Walsh-basis variant: 128 threads, no tensor memory; at most 4 CTAs per
-  // SM (its launch bounds), 3 beside k_force_gen
+  // Walsh-basis variant: 128 threads, no tensor memory, no staging of the
+  // cell forces; at most 5 CTAs per SM (its launch bounds), and room for
+  // one k_force_gen CTA beside them
   ctx->wt_smem = wt_layout(recmax, nnmax).total;
-  int per_sm_w = (int)((228u * 1024u) / (ctx->wt_smem + 1024u));
-  per_sm_w = std::max(1, std::min(per_sm_w, gen.empty() ? 4 : 3));
+  const size_t gen_room = gen.empty() ? 0 : ctx->gen_smem + 1024u;
+  int per_sm_w = (int)((228u * 1024u - gen_room) / (ctx->wt_smem + 1024u));
+  per_sm_w = std::max(1, std::min(per_sm_w, 5));
   ctx->wt_grid = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)nsm * per_sm_w));
   if (ctx->tc_smem[0] > 227u * 1024u) {
     err = "tensor-core tile needs more than 227 KB of shared memory";
