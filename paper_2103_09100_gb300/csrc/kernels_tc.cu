@@ -479,7 +479,7 @@ __device__ __forceinline__ void wht8f(float *x) {
       }
 }
 
-__global__ void __launch_bounds__(WT_THREADS, 5)
+__global__ void __launch_bounds__(WT_THREADS, 6)
     k_force_wht32(const TcTile *__restrict__ tiles, int ntiles, const uint8_t *__restrict__ recs,
                   const WhtF Kw, const float *__restrict__ u, float *__restrict__ f4, LoadTable Ld,
                   const int64_t *__restrict__ d_step, double dt, int32_t *flags, int rec_max,
@@ -1043,12 +1043,11 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   per_sm = std::max(1, std::min(per_sm, gen.empty() ? 4 : 3));
   ctx->tc_grid[0] = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)nsm * per_sm));
   // Walsh-basis variant: 128 threads, no tensor memory, no staging of the
-  // cell forces; at most 5 CTAs per SM (its launch bounds), and room for
-  // one k_force_gen CTA beside them
+  // cell forces; 6 CTAs per SM (its launch bounds; 4, 5 and 7 measured
+  // 1-2 % slower on the cavity cube, k_force_gen filling in as they finish)
   ctx->wt_smem = wt_layout(recmax, nnmax).total;
-  const size_t gen_room = gen.empty() ? 0 : ctx->gen_smem + 1024u;
-  int per_sm_w = (int)((228u * 1024u - gen_room) / (ctx->wt_smem + 1024u));
-  per_sm_w = std::max(1, std::min(per_sm_w, 5));
+  int per_sm_w = (int)((228u * 1024u) / (ctx->wt_smem + 1024u));
+  per_sm_w = std::max(1, std::min(per_sm_w, 6));
   ctx->wt_grid = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)nsm * per_sm_w));
   if (ctx->tc_smem[0] > 227u * 1024u) {
     err = "tensor-core tile needs more than 227 KB of shared memory";
