@@ -52,10 +52,11 @@ FP64_PEAK_TOPS = 2 * 152 * 2.07e9 / 1e12   # FP64 pipe operations per second (T)
 # DRAM bytes (read + write) of one force launch pair on the cavity cube, from
 # the ncu captures summarised in profiles/: the tensor-core kernel's pair
 # (k_force_tc 67.6 MB + k_force_gen 13.1 MB, k_force_tc_mixed_cavity_cube.md)
-# and the Walsh kernel's pair (None until captured); valid for those
+# and the Walsh kernel's pair (k_force_wht32 67.6 MB + k_force_gen 13.1 MB,
+# k_force_wht32_mixed_cavity_cube.md); valid for those
 # kernel versions
 FORCE_TRAFFIC_MIXED_TC = 80.7e6
-FORCE_TRAFFIC_MIXED_WALSH = None
+FORCE_TRAFFIC_MIXED_WALSH = 80.7e6
 
 
 def dist_env():
