@@ -342,8 +342,9 @@ int sbx_lanczos(sbx_ctx *ctx, int64_t k, const double *v0, double *alpha, double
 
 /*
  * sbx_set_mixed_kernel: mixed form (one load case) only -- which kernel
- * applies K_p to the regular 8-node cells (the other patterns always run
- * on the FP32 SIMT pattern kernel): SBX_MIXED_TENSOR (TF32x3 on the tensor
+ * applies K_p to the regular 8-node cells in the element-by-element
+ * internal force (Eq. Rintep; the other patterns always run on the FP32
+ * SIMT pattern kernel): SBX_MIXED_TENSOR (TF32x3 on the tensor
  * cores, tcgen05, accumulators in tensor memory) or SBX_MIXED_WALSH (FP32
  * SIMT in the Walsh basis of the cell's corners, where K_p is eight 3 x 3
  * blocks).  Both take the same tiles, differences to slot 0 and node sums;
