@@ -326,6 +326,7 @@ int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vecto
   const uint32_t tsz = ctx->prec == SBX_PREC_FP64 ? 8u : 4u;
   std::vector<uint8_t> recs;
   std::vector<TcTile> tiles[3];
+  std::vector<int64_t> work[3];   // multiply-adds per load case of each tile
   int nnmax[3] = {1, 1, 1}, recmax[3] = {16, 16, 16};
   std::vector<std::pair<int32_t, int32_t>> v;
   for (int p = 0; p < P; ++p) {
@@ -370,6 +371,7 @@ int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vecto
       t.rec_bytes = (int32_t)R.bytes;
       t.pat = p;
       tiles[cls].push_back(t);
+      work[cls].push_back((int64_t)nc * m * m);
       nnmax[cls] = std::max(nnmax[cls], nn);
       recmax[cls] = std::max(recmax[cls], (int)R.bytes);
       c0 += nc;
@@ -392,6 +394,17 @@ int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vecto
     return SBX_OK;
   };
   if (int rc = up(&ctx->d_b_rec, recs)) return rc;
+  // heaviest tiles first within a class (CTAs are issued in order: long ones
+  // start early, short ones fill the end)
+  for (int c = 0; c < 3; ++c) {
+    std::vector<size_t> ord(tiles[c].size());
+    for (size_t q = 0; q < ord.size(); ++q) ord[q] = q;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](size_t a, size_t b) { return work[c][a] > work[c][b]; });
+    std::vector<TcTile> sorted;
+    for (size_t q : ord) sorted.push_back(tiles[c][q]);
+    tiles[c].swap(sorted);
+  }
   for (int c = 0; c < 3; ++c) {
     if (int rc = up(&ctx->d_b_tiles[c], tiles[c])) return rc;
     ctx->n_b_tiles[c] = (int)tiles[c].size();

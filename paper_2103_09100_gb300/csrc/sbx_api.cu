@@ -511,6 +511,12 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   std::vector<Tile> rest;
   for (const Tile &t : tiles)
     if (t.pat != wht_pat) rest.push_back(t);
+  // heaviest first (m_p^2 per cell): the CTAs are issued in order, so long
+  // ones start early and short ones fill the end
+  std::stable_sort(rest.begin(), rest.end(), [&](const Tile &a, const Tile &b) {
+    const int64_t na = ctx->pat_nodes[a.pat], nb = ctx->pat_nodes[b.pat];
+    return na * na * a.ncell > nb * nb * b.ncell;
+  });
 
   free_mesh(ctx);
   int rc = SBX_OK;
