@@ -9,9 +9,14 @@
 // 16-byte vector reduction.  No FP64 arithmetic runs per node or cell
 // (GB300's FP64 pipe is ~1/64 of FP32).
 //
-// Two kernels:
-//   k_force_tc   the 8-node cell with the identity op (the bulk of a refined
-//                octree) on the 5th-generation tensor cores: a persistent,
+// Three kernels:
+//   k_force_wht32 (default for) the 8-node cell with the identity op (the
+//                bulk of a refined octree): the same tiles and pipeline as
+//                k_force_tc below, one thread per cell, and K_p applied in
+//                the Walsh basis of the cell's corners, where it is eight
+//                3 x 3 blocks (FP32 SIMT; no tensor memory).
+//   k_force_tc   the same cells on the 5th-generation tensor cores
+//                (sbx_set_mixed_kernel): a persistent,
 //                software-pipelined kernel over tiles of up to 128 cells.
 //                The record of tile i+2 streams in by one 1-D bulk copy (TMA
 //                engine, completion on an mbarrier) while tile i is
@@ -36,7 +41,8 @@
 // group (LBO = 128 B, SBO = nK * 128 B).  TMEM columns: D 0..31, A_hi
 // 32..55, A_lo 64..87.
 //
-// Tile records of k_force_tc (every part padded to 16 bytes), two kinds:
+// Tile records of k_force_tc and k_force_wht32 (every part padded to 16
+// bytes), two kinds:
 //  brick (kind 1): 128 same-size cells forming a complete 4 x 4 x 8 block,
 //   cell c at (c & 3, (c >> 2) & 3, c >> 4), nodes on the 5 x 5 x 9 lattice,
 //   node (a, b, c) = index a + 5 b + 25 c; slot k = corner (k & 1, k >> 1 & 1,
