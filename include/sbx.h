@@ -350,7 +350,8 @@ int sbx_lanczos(sbx_ctx *ctx, int64_t k, const double *v0, double *alpha, double
  * blocks).  Both take the same tiles, differences to slot 0 and node sums;
  * the Walsh kernel is available (and the default) when the 8-node
  * pattern's K_p passed the block check at mesh_upload.
- *   Errors: SBX_EINVAL (ctx NULL, unknown kind, Walsh not available).
+ *   Errors: SBX_EINVAL (ctx NULL, unknown kind, Walsh not available, a
+ *   mesh in another form).
  */
 #define SBX_MIXED_TENSOR 0
 #define SBX_MIXED_WALSH  1

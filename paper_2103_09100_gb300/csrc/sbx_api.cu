@@ -1044,6 +1044,8 @@ int sbx_set_mixed_kernel(sbx_ctx *ctx, int kind) {
   if (!ctx) return SBX_EINVAL;
   if (kind != SBX_MIXED_TENSOR && kind != SBX_MIXED_WALSH)
     return fail(ctx, SBX_EINVAL, "unknown mixed kernel");
+  if (ctx->have_mesh && (ctx->prec != SBX_PREC_MIXED || ctx->B != 1))
+    return fail(ctx, SBX_EINVAL, "sbx_set_mixed_kernel applies to the mixed form with one load case");
   if (kind == SBX_MIXED_WALSH && ctx->wht_pat < 0)
     return fail(ctx, SBX_EINVAL, "no Walsh blocks for this mesh");
   const bool w = kind == SBX_MIXED_WALSH;
