@@ -127,6 +127,22 @@ def test_lumping_conserves_mass_per_direction(mask):
         assert abs(c.M_lump[d::3].sum() - 3.0 * 0.125) < 1e-13
 
 
+@pytest.mark.parametrize("mask", MASKS)
+def test_lumped_mass_first_moment_is_the_centroid(mask):
+    # With the direction-wise row sums of Sec. 3.3, sum_i m_i,d x_i equals the
+    # kinetic cross term of the constant and the linear field d, i.e.
+    # rho * integral of x over the cell: rho h^3 (x_c + shift) for the cube
+    # [-h/2, h/2]^3 moved by `shift`.  Catches lumped masses handed to the
+    # wrong node, which the conservation check above does not.
+    h, rho = 0.5, 3.0
+    c = sbfem.solve_cell(mask, h=h, rho=rho)
+    shift = np.array([0.3, -0.7, 1.1])
+    X = _nodes(mask, h) + shift[None, :]
+    for d in range(3):
+        mom = c.M_lump[d::3] @ X
+        assert np.abs(mom - rho * h ** 3 * shift).max() < 1e-13
+
+
 def test_displacement_exponents():
     # three translations (s = 0) and nine linear fields (s = 1) are among the
     # bounded modes of every pattern
