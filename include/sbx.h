@@ -7,11 +7,11 @@
  *   sbx_create        -- bind a CUDA device and stream
  *   set_patterns      -- master-cell stiffness K_p and lumped mass (Table: K_e, M_e)
  *   mesh_upload       -- cells: pattern T, transform, DOF vector V, edge length S,
- *                        modulus, density; Dirichlet DOFs Gamma_D (Alg. 1 lines 1-6)
+ *                        modulus, density; Dirichlet DOFs Gamma_D (Alg. 1, set-up)
  *   set_load          -- point loads Gamma_N with a time function (Sec. 5, Eqs.
  *                        Ricker, Triangle, Lamb)
  *   set_initial       -- U_0, Udot_0 and the fictitious U_-1 (Eq. D0)
- *   step_n            -- n central-difference steps (Alg. 1 lines 8-20;
+ *   step_n            -- n central-difference steps (Alg. 1, time loop;
  *                        Eqs. Rintep, DnMdiag)
  *   read_field / write_field -- state in and out (checkpoint / resume)
  *
@@ -55,11 +55,13 @@ typedef struct sbx_ctx sbx_ctx;
 
 /* precision modes of mesh_upload (the displacement history is FP64 in all) */
 #define SBX_PREC_FP64   0  /* K_p u_e in FP64 (DFMA)                           */
-#define SBX_PREC_MIXED  1  /* 8-node cells: K_p u_e as three TF32 tensor-core
-                              products of split operands, FP32 accumulation
-                              (tcgen05); other patterns: FP32 FFMA.  Both on
-                              each cell's displacements relative to its
-                              slot-0 node                                     */
+#define SBX_PREC_MIXED  1  /* 8-node cells: K_p u_e in FP32 in the Walsh
+                              basis of the corners (default), or as three
+                              TF32 tensor-core products of split operands
+                              with FP32 accumulation (tcgen05), chosen by
+                              sbx_set_mixed_kernel; other patterns: FP32
+                              FFMA.  All on each cell's displacements
+                              relative to its slot-0 node                     */
 #define SBX_PREC_FP32   2  /* K_p u_e in FP32 (FFMA), FP64 scale and update   */
 
 /* fields of read_field / write_field */
@@ -109,7 +111,7 @@ int set_patterns(sbx_ctx *ctx, int n_patterns, const int32_t *n_nodes,
                  const double *K_packed, const double *Mlump_packed);
 
 /*
- * mesh_upload: the octree mesh of Alg. 1 lines 1-6 (Table: V, T, S, M_diag,
+ * mesh_upload: the octree mesh of Alg. 1's set-up (Table: V, T, S, M_diag,
  * Gamma_D).  Builds the lumped global mass M_diag = sum_e rho_e h_e^3 M_p(e)
  * (in cell components) and allocates the state (U_n = U_{n-1} = 0).
  *   n_nodes, n_cells  N and C.
@@ -299,7 +301,7 @@ int sbx_touch(sbx_ctx *ctx);
 /*
  * sbx_set_receivers: record a time history of the displacement at n_rec
  * entries of the state array (receivers, as in Sec. 5's measured
- * responses) after every step that sbx_step_n takes from now on, for at
+ * responses) after every step that step_n takes from now on, for at
  * most max_steps steps.  rec_idx[r] indexes the state array U_n of this
  * context: DOF 3 node + d, batched (3 node + d) B + b; host or device
  * pointer, copied.  n_rec = 0 turns recording off.  Recording costs one

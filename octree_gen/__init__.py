@@ -1,6 +1,6 @@
 """Seeded synthetic 2:1-balanced octree meshes (inputs only).
 
-This module produces the *input mesh* of Algorithm 1 (line 1) and nothing
+This module produces the *input mesh* of Algorithm 1 and nothing
 else: cells, their hanging-node masks, node ids and coordinates, material
 fields, fixed nodes and point loads.  It holds none of the method's
 arithmetic (no stiffness, mass, pattern reduction or time stepping); both

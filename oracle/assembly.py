@@ -96,7 +96,7 @@ def _mask_groups(mesh):
 
 
 def lumped_mass(mesh) -> np.ndarray:
-    """Global diagonal mass M_diag (Algorithm 1, line 5): sum over cells of
+    """Global diagonal mass M_diag (Algorithm 1, set-up): sum over cells of
     rho_e h_e^3 diag(T^T M_lump,p T), added in through each cell's DOFs."""
     M = np.zeros(mesh.n_dof)
     for mask, cells in _mask_groups(mesh).items():

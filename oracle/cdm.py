@@ -3,7 +3,7 @@
 Part of the FP64 oracle (test infrastructure; see ``oracle/__init__``).
 
 ``build()`` compiles ``cdm.c`` with gcc into ``oracle/_build/libcdm.so``.
-``Problem`` gathers what Algorithm 1 lines 1-7 prepare: per-cell pattern,
+``Problem`` gathers what the set-up stage of Algorithm 1 prepares: per-cell pattern,
 scale s_e = E_e h_e, DOF lists, the transform tables, the global diagonal
 mass, dt^2 M^-1 with zeros on fixed DOFs (reading: Dirichlet DOFs are held
 at zero), and the point loads.  ``run`` steps the C solver.  ``run_sparse``
@@ -81,7 +81,7 @@ class Problem:
 
 
 def make_problem(mesh, dt=None, dt_factor=0.5, alpha=0.0, sources=None, rhs=0) -> Problem:
-    """Algorithm 1 lines 1-7 for ``mesh``.  ``dt`` defaults to
+    """The set-up stage of Algorithm 1 for ``mesh``.  ``dt`` defaults to
     dt_factor * dt_cr (Eqs. tcr, tcr_scale).  Only sources of load case
     ``rhs`` are applied."""
     tab = assembly.pattern_tables(mesh)

@@ -1,4 +1,4 @@
-"""High-level set-up of the GPU explicit solver (Algorithm 1 lines 1-7).
+"""High-level set-up of the GPU explicit solver (the set-up stage of Algorithm 1).
 
 ``Solver`` takes a balanced octree mesh as plain arrays (26 node slots per
 cell, 12-bit hanging-node mask, edge length, modulus, density, fixed nodes,

@@ -1,4 +1,4 @@
-"""Receiver time histories recorded on the GPU during sbx_step_n (one row per
+"""Receiver time histories recorded on the GPU during step_n (one row per
 step, U after that step at the chosen state-array entries) against the FP64
 oracle's receiver output of the same run: bit-for-bit up to FP64 rounding in
 the FP64 form (1e-12 of the largest recorded value), 1e-5 in the mixed form,
