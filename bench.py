@@ -83,6 +83,17 @@ def algorithmic_bytes(mesh, nper, B=1):
     return step, force
 
 
+def update_bytes_moved(mesh, precision):
+    """Bytes the update kernel of one load case moves per step in its own
+    layout.  Mixed form, per node: w, U_n, U_{n-1} read and U_{n+1} written
+    (4 x 24 B), the FP32 force read and cleared (2 x 16 B), the (hi, lo) FP32
+    pairs of U_{n+1} written (24 B): 152 B.  FP64 / FP32 forms: w, f, U_n,
+    U_{n-1} read, U_{n+1} written, f cleared: 6 x 8 B per DOF."""
+    if precision == "mixed":
+        return 152 * (mesh.n_dof // 3)
+    return 48 * mesh.n_dof
+
+
 def contraction_flops(nper, B=1):
     m = 3 * nper.astype(np.float64)
     return float(np.sum(2 * m * m)) * B
@@ -314,6 +325,9 @@ def main():
     roof.update({"algorithmic_bytes_per_launch": bytes_force, "force_ms": t_force * 1e3,
                  "update_ms": t_update * 1e3,
                  "update_hbm_frac": (32 * mesh.n_dof / t_update / 1e9) / pk["hbm_gbs"],
+                 "update_bytes_moved": update_bytes_moved(mesh, args.precision),
+                 "update_moved_frac": (update_bytes_moved(mesh, args.precision) / t_update / 1e9)
+                 / pk["hbm_gbs"],
                  "step_bytes": bytes_step,
                  "step_hbm_frac": (bytes_step / (t_force + t_update) / 1e9) / pk["hbm_gbs"]})
 

@@ -55,3 +55,14 @@ def test_algorithmic_bytes():
     cell = 3 * 9 + 4 * (8 + 8 + 11)
     assert force == 8 * 300 + cell
     assert step == 24 * 300 + 8 * 300 + cell
+
+
+def test_update_bytes_moved():
+    B = _bench()
+
+    class M:
+        n_dof = 300
+
+    assert B.update_bytes_moved(M, "mixed") == 152 * 100
+    assert B.update_bytes_moved(M, "fp64") == 48 * 300
+    assert B.update_bytes_moved(M, "fp32") == 48 * 300
