@@ -188,6 +188,50 @@ def oracle_reference(mesh, dt, n_steps, rhs=0, threads=None):
     return u, time.perf_counter() - t
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or 'unknown'."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_cpu_baseline(mesh, budget_s=15.0, single_steps=3):
+    """The FP64 C oracle as it stands, timed on the host cores on a bounded
+    sample of the workload: about budget_s seconds of CDM steps with OpenMP
+    over all cores, then single_steps steps on one thread."""
+    from oracle import cdm
+    threads = os.cpu_count() or 1
+    P = cdm.make_problem(mesh)
+    u, up = cdm.initial_state(P)
+    t = time.perf_counter()
+    u, up, _, _ = cdm.run(P, 2, u, up, threads=threads)
+    per = (time.perf_counter() - t) / 2
+    n = max(2, int(budget_s / max(per, 1e-6)))
+    t = time.perf_counter()
+    cdm.run(P, n, u, up, n0=2, threads=threads)
+    el = time.perf_counter() - t
+    t = time.perf_counter()
+    cdm.run(P, single_steps, u, up, n0=2, threads=1)
+    el1 = time.perf_counter() - t
+    return {"value": mesh.n_dof * n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d CDM steps (steps 2..%d) of the full %s workload, FP64 C oracle, "
+                      "OpenMP %d threads; single thread: %d steps"
+                      % (n, n + 1, mesh.name, threads, single_steps),
+            "single_thread_value": mesh.n_dof * single_steps / el1, "cpu_model": cpu_model()}
+
+
 def gpu_after(S, n_steps, L):
     S.initial()
     S.step(n_steps)
@@ -215,7 +259,8 @@ def run_reference(args):
            "data": "synthetic", "config": {"workload": mesh.name, "cells": mesh.n_cells,
                                            "dof": mesh.n_dof, "precision": "fp64 (oracle)"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                            "sample": "%d full CDM steps of the workload" % args.steps},
+                            "sample": "%d full CDM steps of the workload" % args.steps,
+                            "cpu_model": cpu_model()},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -462,21 +507,7 @@ def main():
         S.close()
 
     if rank == 0 and not args.no_cpu_baseline:
-        from oracle import cdm
-        threads = os.cpu_count() or 1
-        P = cdm.make_problem(mesh)
-        u, up = cdm.initial_state(P)
-        t = time.perf_counter()
-        u, up, _, _ = cdm.run(P, 2, u, up, threads=threads)
-        per = (time.perf_counter() - t) / 2
-        n = max(2, int(15.0 / max(per, 1e-6)))
-        t = time.perf_counter()
-        cdm.run(P, n, u, up, n0=2, threads=threads)
-        el = time.perf_counter() - t
-        out["cpu_baseline"] = {"value": mesh.n_dof * n / el, "unit": UNIT, "cores": threads,
-                               "kind": "oracle",
-                               "sample": "%d CDM steps (steps 2..%d) of the full cavity workload, "
-                                         "FP64 C oracle, OpenMP %d threads" % (n, n + 1, threads)}
+        out["cpu_baseline"] = oracle_cpu_baseline(mesh)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

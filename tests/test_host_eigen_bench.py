@@ -66,3 +66,15 @@ def test_update_bytes_moved():
     assert B.update_bytes_moved(M, "mixed") == 152 * 100
     assert B.update_bytes_moved(M, "fp64") == 48 * 300
     assert B.update_bytes_moved(M, "fp32") == 48 * 300
+
+
+def test_oracle_cpu_baseline_on_a_small_mesh():
+    import octree_gen as og
+    B = _bench()
+    mesh = og.config_corner_cube()
+    cb = B.oracle_cpu_baseline(mesh, budget_s=0.2, single_steps=2)
+    assert cb["kind"] == "oracle" and cb["unit"] == B.UNIT
+    assert cb["cores"] == (os.cpu_count() or 1)
+    assert cb["value"] > 0 and cb["single_thread_value"] > 0
+    assert isinstance(cb["cpu_model"], str) and cb["cpu_model"]
+    assert mesh.name in cb["sample"]
