@@ -78,6 +78,41 @@ def test_sdof_stability_limit():
     assert np.abs(bad).max() > 1e6
 
 
+@pytest.mark.parametrize("alpha", [0.0, 0.8])
+def test_rigid_motion_from_eq_d0_start(alpha):
+    # A free mesh moving as a rigid translation c + t b: K annihilates it, so
+    # every DOF follows the SDOF recurrence without stiffness,
+    # (1 + a dt/2) u_{n+1} - 2 u_n + (1 - a dt/2) u_{n-1} = 0, from the
+    # Eq. (D0) start u_-1 = c - dt b + dt^2/2 (-a b).  Undamped that is
+    # exact linear motion u_n = c + n dt b; damped, u_n = A + B r^n with
+    # r = (1 - a dt/2) / (1 + a dt/2).  Pins initial_state's velocity and
+    # damping terms and their signs.
+    m = og.tiny_refined(4)
+    m.fixed_nodes = np.zeros(0, np.int64)
+    m.sources = []
+    P = cdm.make_problem(m, dt_factor=0.5, alpha=alpha)
+    assert len(P.fixed) == 0
+    c = np.array([0.3, -0.2, 0.5])
+    b = np.array([1.0, 0.4, -0.7])
+    nn = m.n_dof // 3
+    u0, um1 = cdm.initial_state(P, np.tile(c, nn), np.tile(b, nn))
+    n = 60
+    uN, uNm1, _, _ = cdm.run(P, n, u0, um1)
+    dt = P.dt
+    if alpha == 0.0:
+        exact_n, exact_nm1 = c + n * dt * b, c + (n - 1) * dt * b
+    else:
+        r = (1 - 0.5 * alpha * dt) / (1 + 0.5 * alpha * dt)
+        cm1 = c - dt * b - 0.5 * dt * dt * alpha * b
+        # A + B = c, A + B / r = cm1
+        B = (c - cm1) / (1 - 1 / r)
+        A = c - B
+        exact_n, exact_nm1 = A + B * r ** n, A + B * r ** (n - 1)
+    scale = np.abs(exact_n).max()
+    assert np.abs(uN.reshape(-1, 3) - exact_n[None, :]).max() < 1e-10 * scale
+    assert np.abs(uNm1.reshape(-1, 3) - exact_nm1[None, :]).max() < 1e-10 * scale
+
+
 @pytest.fixture(scope="module")
 def tiny_problem():
     m = og.tiny_refined(2)
