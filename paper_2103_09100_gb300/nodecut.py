@@ -133,19 +133,53 @@ class NodeCutSolver:
         self.stream.synchronize()
         return self.S.field(which)
 
+    def sync(self):
+        """Wait for this part's work on the device (library and sum streams)."""
+        self.torch.cuda.synchronize()
+
     def close(self):
         self.S.close()
 
 
-def step_distributed(engine, n, group=None):
-    """n steps of one rank's engine; the interface sum is an all_reduce."""
+def step_distributed(engine, n, group=None, times=None):
+    """n steps of one rank's engine; the interface sum is an all_reduce.
+
+    times: optional dict in which the split of the step time that Sec. 4's
+    timing study reports per rank accumulates, in seconds on the host
+    clock: 't_C' the rank's own work (force and update), 't_W' the
+    interface sum (pack, all_reduce, unpack, including the wait for the
+    slowest rank).  The engine is then synchronised between the phases
+    (its ``sync()``, if it has one), which gives up their overlap; without
+    ``times`` nothing is synchronised."""
     import torch.distributed as dist
+    if times is None:
+        for _ in range(n):
+            if engine.force():
+                buf = engine.pack_force()
+                dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+                engine.unpack_force(buf)
+            engine.update()
+        return
+    import time
+    sync = getattr(engine, "sync", None) or (lambda: None)
+    times.setdefault("t_C", 0.0)
+    times.setdefault("t_W", 0.0)
     for _ in range(n):
-        if engine.force():
+        t0 = time.perf_counter()
+        fresh = engine.force()
+        sync()
+        t1 = time.perf_counter()
+        if fresh:
             buf = engine.pack_force()
             dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
             engine.unpack_force(buf)
+            sync()
+        t2 = time.perf_counter()
         engine.update()
+        sync()
+        t3 = time.perf_counter()
+        times["t_C"] += (t1 - t0) + (t3 - t2)
+        times["t_W"] += t2 - t1
 
 
 def step_together(engines, n):

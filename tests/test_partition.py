@@ -190,8 +190,10 @@ def _rank_main(rank, world, port, out_dir, n_steps):
         e = OracleEngine(m, parts[rank])
         u0 = np.random.default_rng(2).standard_normal(m.n_dof) * 1e-3
         dt = nodecut.setup_distributed(e, 0.5, u0=u0)
-        nodecut.step_distributed(e, n_steps)
-        np.savez(os.path.join(out_dir, "r%d.npz" % rank), u=e.u, nodes=e.part.nodes, dt=dt)
+        times = {}
+        nodecut.step_distributed(e, n_steps, times=times)
+        np.savez(os.path.join(out_dir, "r%d.npz" % rank), u=e.u, nodes=e.part.nodes, dt=dt,
+                 t_C=times["t_C"], t_W=times["t_W"])
     finally:
         dist.destroy_process_group()
 
@@ -212,6 +214,8 @@ def test_gloo_two_ranks_equal_global_oracle():
     ug = u.reshape(-1, 3)
     for r in res:
         assert np.abs(r["u"].reshape(-1, 3) - ug[r["nodes"]]).max() <= 1e-12 * np.abs(ug).max()
+        # the per-rank split of the step time (Sec. 4): own work and interface sum
+        assert float(r["t_C"]) > 0.0 and float(r["t_W"]) > 0.0
 
 
 def _rank_leaves(rank, world, port, out_dir):
