@@ -296,6 +296,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"],
                     help="headline form on the cavity mesh")
+    ap.add_argument("--mixed-kernel", default="walsh", choices=["walsh", "tensor"],
+                    help="mixed form: kernel for the regular 8-node cells of the headline "
+                         "solver (walsh: Walsh-basis FP32 SIMT, the default; tensor: tcgen05)")
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
@@ -329,6 +332,8 @@ def main():
 
     # ---------------------------------------------------------- headline form
     S = Solver.from_mesh(mesh, precision=args.precision, device=local, stream=stream.cuda_stream)
+    if args.precision == "mixed" and args.mixed_kernel == "tensor":
+        L.sbx_set_mixed_kernel(S.ctx, L.SBX_MIXED_TENSOR)
     S.initial()
     S.step(args.warmup)
     S.sync()
