@@ -15,6 +15,11 @@ through K_e = E_e h_e T_e^T K_p T_e (Eq. KM_scale), hence
     dJ/dE_e = - sum_{n=0}^{N-1} (W lambda_{n+1})_e^T (K_e / E_e) U_{n,e}.
 Every quantity here is plain FP64; the K applications use the oracle's
 element-by-element sum.
+
+``gradient`` keeps every state; ``gradient_checkpointed`` computes the same
+sums for long runs, keeping the state pair (U_{s-1}, U_s) only at every k-th
+step s and stepping each segment forward again, from its pair, just before
+the reverse sweep needs it.  Both sum the same terms in the same order.
 """
 from __future__ import annotations
 
@@ -91,3 +96,53 @@ def misfit_of_moduli(mesh, E, dt, n_steps, rec, data, sources=None):
         return misfit(forward_states(P, n_steps), rec, data)
     finally:
         mesh.E = E0
+
+
+def traces(P, n_steps, rec, threads=1):
+    """U_n[rec] for n = 1..N (rows), forward from rest."""
+    u, up = cdm.initial_state(P)
+    _, _, tr, _ = cdm.run(P, n_steps, u, up, receivers=rec, threads=threads)
+    return tr
+
+
+def gradient_checkpointed(P, n_steps, rec, data, every=64, threads=1):
+    """(J, dJ/dE) as ``gradient``, holding k + 2 states at a time (k = every).
+
+    Forward: from rest, the misfit terms of U_1..U_N and the pairs
+    (U_{s-1}, U_s) for s = 0, k, 2k, ...  Reverse, segment by segment from
+    the last: U_{s0+1}..U_{s0+k} are stepped again from the pair at s0, then
+    for n = s0+k down to s0+1
+        lambda_n = g_n + 2 lambda_{n+1} - K W lambda_{n+1} - lambda_{n+2}
+        dJ/dE   -= (W lambda_n)^T (K_e / E_e) U_{n-1}   (per cell).
+    """
+    if P.alpha != 0.0:
+        raise ValueError("the adjoint is written for the undamped recurrence")
+    rec = np.asarray(rec, np.int64)
+    u, up = cdm.initial_state(P)
+    pairs = {0: (up.copy(), u.copy())}
+    J = 0.0
+    for s0 in range(0, n_steps, every):
+        k = min(every, n_steps - s0)
+        u, up, tr, _ = cdm.run(P, k, u, up, n0=s0, receivers=rec, threads=threads)
+        r = tr - data[s0:s0 + k]
+        J += 0.5 * float(np.sum(r * r))
+        pairs[s0 + k] = (up.copy(), u.copy())
+    W = P.dt2minv
+    everything = np.arange(P.n_dof, dtype=np.int64)
+    lam1 = np.zeros(P.n_dof)
+    lam2 = np.zeros(P.n_dof)
+    grad = np.zeros(P.mesh.n_cells)
+    for s0 in reversed(range(0, n_steps, every)):
+        k = min(every, n_steps - s0)
+        up, u = pairs[s0]
+        # seg[j] = U_{s0 + j - 1}, j = 0..k+1
+        _, _, later, _ = cdm.run(P, k, u, up, n0=s0, receivers=everything, threads=threads)
+        seg = np.concatenate([up[None, :], u[None, :], later], axis=0)
+        for n in range(s0 + k, s0, -1):
+            Un, Unm1 = seg[n - s0 + 1], seg[n - s0]
+            g = np.zeros(P.n_dof)
+            np.add.at(g, rec, Un[rec] - data[n - 1])
+            lam = g + 2.0 * lam1 - cdm.apply_K(P, W * lam1, threads=threads) - lam2
+            grad -= cdm.cell_energy(P, W * lam, Unm1, threads=threads)
+            lam2, lam1 = lam1, lam
+    return J, grad

@@ -98,6 +98,91 @@ int oracle_apply_K(int64_t n_dof, int64_t n_cells,
 }
 
 /*
+ * The same sum with the cells split over n_threads OpenMP threads, each with
+ * its own force buffer, summed afterwards in thread order.
+ */
+int oracle_apply_K_threads(int64_t n_dof, int64_t n_cells,
+                           const int64_t *pat_m, const int64_t *pat_off, const double *kp,
+                           const int64_t *cell_pat, const double *scale,
+                           const int64_t *node_ptr, const int64_t *dofs, const int64_t *tmap,
+                           const int64_t *comp, const int64_t *sign,
+                           const double *u, double *f, int n_threads)
+{
+    Mesh M = {n_dof, n_cells, pat_m, pat_off, kp, cell_pat, scale, node_ptr, dofs, tmap, comp, sign};
+    int nt = n_threads > 1 ? n_threads : 1;
+    if (nt == 1)
+        return oracle_apply_K(n_dof, n_cells, pat_m, pat_off, kp, cell_pat, scale, node_ptr,
+                              dofs, tmap, comp, sign, u, f);
+#ifdef _OPENMP
+    double *buf = (double *)calloc((size_t)n_dof * (size_t)nt, sizeof(double));
+    if (!buf) return 1;
+#pragma omp parallel num_threads(nt)
+    {
+        int t = omp_get_thread_num();
+        double Ke[MAXM * MAXM], ue[MAXM];
+        int64_t c0 = n_cells * t / nt, c1 = n_cells * (t + 1) / nt;
+        internal_force(&M, u, buf + (size_t)t * (size_t)n_dof, c0, c1, Ke, ue);
+    }
+    for (int64_t d = 0; d < n_dof; ++d) {
+        double s = 0.0;
+        for (int t = 0; t < nt; ++t) s += buf[(size_t)t * (size_t)n_dof + d];
+        f[d] = s;
+    }
+    free(buf);
+    return 0;
+#else
+    return 2;
+#endif
+}
+
+/*
+ * Per cell e: out[e] = a_e^T (h_e T_e^T K_p T_e) b_e, the cell's stiffness
+ * divided by its modulus (Eq. KM_scale: K_e = E_e h_e T_e^T K_p T_e) between
+ * the gathered vectors a_e and b_e.  K_e / E_e is built entry by entry as in
+ * internal_force, with h in place of s_e.
+ */
+int oracle_cell_energy(int64_t n_dof, int64_t n_cells,
+                       const int64_t *pat_m, const int64_t *pat_off, const double *kp,
+                       const int64_t *cell_pat, const double *h,
+                       const int64_t *node_ptr, const int64_t *dofs, const int64_t *tmap,
+                       const int64_t *comp, const int64_t *sign,
+                       const double *a, const double *b, double *out, int n_threads)
+{
+    (void)n_dof;
+    int nt = n_threads > 1 ? n_threads : 1;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nt) schedule(static)
+#endif
+    for (int64_t c = 0; c < n_cells; ++c) {
+        double Ke[MAXM * MAXM];
+        int64_t p = cell_pat[c];
+        int64_t mp = pat_m[p];
+        const double *K = kp + pat_off[p];
+        int64_t n0 = node_ptr[c], nn = node_ptr[c + 1] - n0;
+        int64_t m = 3 * nn;
+        const int64_t *cp = comp + 3 * c, *sg = sign + 3 * c;
+        const int64_t *dof = dofs + 3 * n0;
+        for (int64_t i = 0; i < nn; ++i)
+            for (int r = 0; r < 3; ++r)
+                for (int64_t j = 0; j < nn; ++j)
+                    for (int q = 0; q < 3; ++q) {
+                        int64_t row = 3 * tmap[n0 + i] + cp[r];
+                        int64_t col = 3 * tmap[n0 + j] + cp[q];
+                        Ke[(3 * i + r) * m + 3 * j + q] =
+                            h[c] * (double)(sg[r] * sg[q]) * K[row * mp + col];
+                    }
+        double acc = 0.0;
+        for (int64_t k = 0; k < m; ++k) {
+            double row = 0.0;
+            for (int64_t l = 0; l < m; ++l) row += Ke[k * m + l] * b[dof[l]];
+            acc += a[dof[k]] * row;
+        }
+        out[c] = acc;
+    }
+    return 0;
+}
+
+/*
  * n_steps CDM steps starting from step index n0 (time t_n = n dt).
  * u_c = U_n, u_p = U_{n-1} on entry; U_{n0+n_steps}, U_{n0+n_steps-1} on exit.
  * Loads: load_dof[k] receives load_amp[k] * P(t) of wavelet load_wave[k].

@@ -122,15 +122,38 @@ def _mesh_args(P: Problem):
     return keep, args
 
 
-def apply_K(P: Problem, u: np.ndarray) -> np.ndarray:
-    """R_int = sum_e K_e u_e (Eq. Rinte)."""
+def apply_K(P: Problem, u: np.ndarray, threads: int = 1) -> np.ndarray:
+    """R_int = sum_e K_e u_e (Eq. Rinte); threads > 1 splits the cells over
+    OpenMP threads (per-thread sums added in thread order)."""
     lib = _load()
     u = np.ascontiguousarray(u, float)
     f = np.zeros(P.n_dof)
     keep, args = _mesh_args(P)
-    lib.oracle_apply_K(C.c_int64(P.n_dof), C.c_int64(P.mesh.n_cells), *args,
-                       _p(u, C.c_double), _p(f, C.c_double))
+    if threads > 1:
+        rc = lib.oracle_apply_K_threads(C.c_int64(P.n_dof), C.c_int64(P.mesh.n_cells), *args,
+                                        _p(u, C.c_double), _p(f, C.c_double), C.c_int(threads))
+        if rc != 0:
+            raise RuntimeError("oracle_apply_K_threads failed: %d" % rc)
+    else:
+        lib.oracle_apply_K(C.c_int64(P.n_dof), C.c_int64(P.mesh.n_cells), *args,
+                           _p(u, C.c_double), _p(f, C.c_double))
     return f
+
+
+def cell_energy(P: Problem, a: np.ndarray, b: np.ndarray, threads: int = 1) -> np.ndarray:
+    """Per cell e: a_e^T (K_e / E_e) b_e, K_e / E_e = h_e T_e^T K_p T_e
+    (Eq. KM_scale), built entry by entry in C."""
+    lib = _load()
+    a = np.ascontiguousarray(a, float)
+    b = np.ascontiguousarray(b, float)
+    h = np.ascontiguousarray(P.mesh.h, float)
+    out = np.zeros(P.mesh.n_cells)
+    keep, args = _mesh_args(P)
+    args[4] = _p(h, C.c_double)
+    lib.oracle_cell_energy(C.c_int64(P.n_dof), C.c_int64(P.mesh.n_cells), *args,
+                           _p(a, C.c_double), _p(b, C.c_double), _p(out, C.c_double),
+                           C.c_int(threads))
+    return out
 
 
 def external_force(P: Problem, n: int) -> np.ndarray:

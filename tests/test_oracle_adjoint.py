@@ -62,3 +62,37 @@ def test_zero_residual_gives_zero_gradient(case):
     S = adjoint.forward_states(P, N)
     J, g = adjoint.gradient(P, N, rec, S[2:N + 2][:, rec])
     assert J == 0.0 and np.abs(g).max() == 0.0
+
+
+@pytest.mark.parametrize("every", [1, 7, 64, 120, 500])
+@pytest.mark.parametrize("threads", [1, 3])
+def test_checkpointed_adjoint_equals_store_all(case, every, threads):
+    # the long-run form (pairs every k steps, segments stepped again, C
+    # energy terms, threaded K) sums the same terms as the store-all form,
+    # which the central differences above pin
+    m, P, N, rec, data = case
+    J0, g0 = adjoint.gradient(P, N, rec, data)
+    J1, g1 = adjoint.gradient_checkpointed(P, N, rec, data, every=every, threads=threads)
+    assert abs(J1 - J0) <= 1e-12 * J0
+    assert np.abs(g1 - g0).max() <= 1e-11 * np.abs(g0).max()
+
+
+def test_c_energy_terms_and_threaded_K(case):
+    m, P, N, rec, data = case
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal(P.n_dof)
+    b = rng.standard_normal(P.n_dof)
+    e_py = adjoint.cell_energy_terms(P, a, b)
+    e_c = cdm.cell_energy(P, a, b, threads=2)
+    assert np.abs(e_c - e_py).max() <= 1e-13 * np.abs(e_py).max()
+    # a^T K b summed over cells equals a^T (K b)
+    assert abs(np.sum(e_c * m.E) - a @ cdm.apply_K(P, b)) <= 1e-12 * np.abs(e_c * m.E).sum()
+    assert np.abs(cdm.apply_K(P, b, threads=4) - cdm.apply_K(P, b)).max() <= \
+        1e-13 * np.abs(cdm.apply_K(P, b)).max()
+
+
+def test_traces_are_the_states_at_the_receivers(case):
+    m, P, N, rec, data = case
+    S = adjoint.forward_states(P, N)
+    assert np.abs(adjoint.traces(P, N, rec, threads=2) - S[2:N + 2][:, rec]).max() <= \
+        1e-13 * np.abs(S).max()
