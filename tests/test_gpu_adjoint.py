@@ -6,6 +6,7 @@ import pytest
 import octree_gen as og
 from oracle import adjoint as oadj, cdm
 from paper_2103_09100_gb300 import Solver, _lib as L, build
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -42,7 +43,7 @@ def test_adjoint_matches_oracle_fp64(tiny):
     S.initial()
     J, g = S.adjoint(N, rec, data, ckpt_every=16)
     assert abs(J - J0) <= 1e-10 * J0
-    assert np.abs(g - g0).max() <= 1e-9 * np.abs(g0).max()
+    assert rel(g, g0) <= 1e-9
 
 
 @pytest.mark.parametrize("k", [1, 7, 150, 1000])
@@ -54,7 +55,7 @@ def test_checkpoint_interval_does_not_change_the_result(tiny, k):
     S.initial()
     J2, g2 = S.adjoint(N, rec, data, ckpt_every=k)
     assert abs(J2 - J1) <= 1e-12 * J1
-    assert np.abs(g2 - g1).max() <= 1e-12 * np.abs(g1).max()
+    assert rel(g2, g1) <= 1e-12
     # the state is back at rest afterwards
     assert np.abs(S.field(L.SBX_U_N)).max() == 0.0
 
@@ -88,50 +89,4 @@ def test_autograd_function(tiny):
     J = gadj.misfit(E, S, N, rec, data, ckpt_every=32)
     (2.0 * J).backward()
     _, g0 = oadj.gradient(P, N, rec, data)
-    assert np.abs(E.grad.numpy() - 2 * g0).max() <= 1e-9 * np.abs(2 * g0).max()
-
-
-def test_receiver_cube_fp32_adjoint_vs_fp64_and_fd():
-    # full size: ~100k cells, 2000 steps, 256 receivers, checkpoint every 64;
-    # the FP32-contraction adjoint against the FP64 one, and the FP64 one
-    # against FP64 central differences on 4 cells
-    m = og.config_receiver_cube()
-    S64 = Solver.from_mesh(m, precision="fp64")
-    N = 2000
-    rec = 3 * np.array(m.meta["receivers"], np.int64) + 2
-    # observed traces from moduli with a +10 % Gaussian blob under the source
-    S = 2 ** (m.lmax - m.level.astype(np.int64))
-    c = (m.anchor + 0.5 * S[:, None]) * m.h_finest
-    blob = np.exp(-np.sum((c - np.array([0.5, 0.5, 0.7])) ** 2, 1) / (2 * 0.15 ** 2))
-    S64.set_modulus(m.E * (1 + 0.1 * blob))
-    S64.initial()
-    hist = np.zeros((N, len(rec)))
-    u = np.empty(S64.n_dof)
-    for n in range(N):
-        S64.step(1)
-        hist[n] = S64.field(L.SBX_U_N, u)[rec]
-    S64.set_modulus(m.E)
-    S32 = Solver.from_mesh(m, precision="fp32", dt=S64.dt)
-    S32.initial()
-    J32, g32 = S32.adjoint(N, rec, hist, ckpt_every=64)
-    S64.initial()
-    J64, g64 = S64.adjoint(N, rec, hist, ckpt_every=64)
-    rel = np.abs(g32 - g64).max() / np.abs(g64).max()
-    print("receiver cube: J fp64 %.6e fp32 %.6e, max |g32 - g64| / max |g64| = %.3e"
-          % (J64, J32, rel))
-    assert abs(J32 - J64) <= 1e-4 * J64
-    assert rel < 1e-3
-
-    def J_of(E):
-        S64.set_modulus(E)
-        S64.initial()
-        J, _ = S64.adjoint(N, rec, hist, ckpt_every=64)
-        return J
-
-    order = np.argsort(-np.abs(g64))
-    for e in [order[0], order[10], order[100], order[1000]]:
-        eps = 1e-6 * m.E[e]
-        Ep = m.E.copy(); Ep[e] += eps
-        Em = m.E.copy(); Em[e] -= eps
-        fd = (J_of(Ep) - J_of(Em)) / (2 * eps)
-        assert abs(g64[e] - fd) <= 1e-5 * np.abs(g64).max(), (e, g64[e], fd)
+    assert rel(E.grad.numpy(), 2 * g0) <= 1e-9

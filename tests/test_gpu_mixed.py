@@ -7,6 +7,7 @@ import pytest
 import octree_gen as og
 from oracle import cdm
 from paper_2103_09100_gb300 import Solver, _lib as L, build
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -17,8 +18,6 @@ def _built():
     L.load()
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])

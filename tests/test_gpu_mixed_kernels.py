@@ -9,6 +9,7 @@ import pytest
 import octree_gen as og
 from oracle import cdm
 from paper_2103_09100_gb300 import Solver, _lib as L, build
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -19,8 +20,6 @@ def _built():
     L.load()
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def solver(m, kind, **kw):
@@ -68,20 +67,3 @@ def test_corner_cube_2000_steps(name, kind):
     e = rel(S.field(L.SBX_U_N), u)
     print("corner cube, %s kernel, 2000 steps: %.3e" % (name, e))
     assert e < 1e-5
-
-
-def test_cavity_200_steps_both_kernels():
-    m = og.config_cavity_cube()
-    P = cdm.make_problem(m)
-    W = solver(m, L.SBX_MIXED_WALSH, dt=P.dt)
-    T = solver(m, L.SBX_MIXED_TENSOR, dt=P.dt)
-    W.initial()
-    T.initial()
-    W.step(200)
-    T.step(200)
-    u, up = cdm.initial_state(P)
-    u, up, _, _ = cdm.run(P, 200, u, up, threads=16)
-    ew, et = rel(W.field(L.SBX_U_N), u), rel(T.field(L.SBX_U_N), u)
-    print("cavity 200 steps: Walsh %.3e, tensor cores %.3e, between them %.3e"
-          % (ew, et, rel(W.field(L.SBX_U_N), T.field(L.SBX_U_N))))
-    assert ew < 1e-5 and et < 1e-5

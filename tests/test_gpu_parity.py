@@ -10,6 +10,7 @@ import pytest
 import octree_gen as og
 from oracle import cdm, cube, sbfem
 from paper_2103_09100_gb300 import Solver, _lib as L, build
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -20,8 +21,6 @@ def _built():
     L.load()
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def _solver(mesh, P, precision="fp64", alpha=0.0):
@@ -93,6 +92,24 @@ def test_corner_cube_damped_fp64():
     S = _solver(m, P, alpha=0.3)
     worst, _ = _run_pair(m, P, S, 300, chunk=75)
     assert worst < 1e-12
+
+
+@pytest.mark.parametrize("wave, ncyc", [("triangle", 5.0), ("sine_burst", 3.0)])
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_triangle_and_sine_burst_loads(wave, ncyc, prec, tol):
+    # the point-load time functions of Eqs. (Triangle) and (Lamb) through
+    # set_load, two load points with different directions, 600 steps
+    m = og.config_corner_cube()
+    t1 = og.ricker_t1_for_mesh(m, 4.0)
+    a = og.nearest_node(m, (0.5, 0.5, 1.0))
+    b = og.nearest_node(m, (0.25, 0.75, 1.0))
+    m.sources = [og.point_source(a, (0, 0, -1), t1, P0=2.0, wavelet=wave, n_cycles=ncyc),
+                 og.point_source(b, (1, -0.5, -0.2), 0.6 * t1, wavelet=wave, n_cycles=ncyc)]
+    P = cdm.make_problem(m)
+    S = _solver(m, P, precision=prec)
+    worst, _ = _run_pair(m, P, S, 600, chunk=150)
+    print("corner cube, %s load, %s: max rel error over 600 steps %.3e" % (wave, prec, worst))
+    assert worst < tol
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 65, 97])
