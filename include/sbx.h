@@ -178,6 +178,18 @@ int set_initial(sbx_ctx *ctx, const double *u0, const double *v0,
  */
 int step_n(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha);
 
+/*
+ * sbx_prepare_steps: build, without running them, the CUDA graphs that a
+ * later step_n(ctx, n_steps, dt, alpha) replays (Alg. 1's time loop is
+ * replayed as graphs of 32 steps plus one graph for the call's remaining
+ * steps), so that the first such call launches no capture.  Graphs are
+ * cached per context until dt, alpha, the receivers or the kernel choice
+ * change.  Enqueues nothing when the graphs exist already.
+ *   Errors: SBX_ESTATE (no mesh), SBX_EINVAL (n_steps < 0, dt <= 0,
+ *   alpha < 0), SBX_ECUDA.
+ */
+int sbx_prepare_steps(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha);
+
 /* Current step index n (the state holds U_n and U_{n-1}). */
 int sbx_get_step(sbx_ctx *ctx, int64_t *n_out);
 /* Set the step index, e.g. after write_field when resuming. */
@@ -388,6 +400,26 @@ int sbx_set_mass(sbx_ctx *ctx, const double *mass);
 int sbx_query(sbx_ctx *ctx, int what, int64_t *out);
 
 /*
+ * sbx_set_launch / sbx_get_launch: launch configuration of the force
+ * kernels (no counterpart in the paper: how Eq. Rintep's contraction is
+ * mapped onto the GPU).  The results do not depend on it beyond rounding;
+ * the step graphs are rebuilt after a change.
+ *   SBX_LAUNCH_HANGING_KERNEL      mixed form: the patterns other than the
+ *       identity-op 8-node cell on FP32 SIMT (SBX_HANGING_SIMT, the
+ *       default) or on the tensor cores, TF32 x 3 with FP32 accumulation
+ *       in tensor memory (SBX_HANGING_TENSOR).
+ *   SBX_LAUNCH_WALSH_CTAS_PER_SM   mixed form: resident CTAs per SM of the
+ *       Walsh-basis kernel, 1 .. 8, or 0 for the library's choice.
+ *   Errors: SBX_EINVAL (unknown parameter or value).
+ */
+#define SBX_LAUNCH_HANGING_KERNEL     0
+#define SBX_LAUNCH_WALSH_CTAS_PER_SM  1
+#define SBX_HANGING_SIMT   0
+#define SBX_HANGING_TENSOR 1
+int sbx_set_launch(sbx_ctx *ctx, int what, int value);
+int sbx_get_launch(sbx_ctx *ctx, int what, int *value);
+
+/*
  * sbx_step_static: one undamped explicit step with no external load that
  * allocates nothing.  The paper has no counterpart; this entry point exists
  * for callers that cannot allocate device memory: code that runs while a
@@ -419,7 +451,12 @@ int sbx_query(sbx_ctx *ctx, int what, int64_t *out);
  * overlaps on the GPU (different streams, or different host threads on one
  * device) race and must be ordered by the caller.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) and
- * must come before any stream capture.
+ * the device's SM count, and must come before any stream capture; both stay
+ * cached for the process, so the entry point must not be used again after
+ * a cudaDeviceReset of that device.
+ * The library trusts the device arrays' contents: the caller guarantees
+ * 0 <= node id < n_dof / 3 in conn and 0 <= sym < 48; an id out of range
+ * is an out-of-bounds access on the GPU.
  *   Errors: SBX_EINVAL (sizes, NULL pointers, dt <= 0), SBX_ECUDA.
  */
 #define SBX_STATIC_MAX_DOF      (4 * 1024 * 1024)

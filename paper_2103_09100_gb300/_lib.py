@@ -28,7 +28,10 @@ EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patte
            "read_field", "write_field", "sbx_profile", "sbx_query", "sbx_step_static",
            "set_modulus", "sbx_adjoint", "sbx_force", "sbx_update", "sbx_field_ptr", "sbx_touch",
            "sbx_set_mass", "sbx_wait_selftest", "sbx_set_receivers", "sbx_read_history",
-           "sbx_lanczos", "sbx_set_mixed_kernel"]
+           "sbx_lanczos", "sbx_set_mixed_kernel", "sbx_prepare_steps", "sbx_set_launch",
+           "sbx_get_launch"]
+SBX_LAUNCH_HANGING_KERNEL, SBX_LAUNCH_WALSH_CTAS_PER_SM = 0, 1
+SBX_HANGING_SIMT, SBX_HANGING_TENSOR = 0, 1
 SBX_LAYOUT_F64_DOF, SBX_LAYOUT_F32_NODE4, SBX_LAYOUT_F32_DOF = 0, 1, 2
 SBX_Q_KERNELS_PER_STEP, SBX_Q_FORCE_LAUNCHES, SBX_Q_TILES, SBX_Q_BRICK_TILES = 0, 1, 2, 3
 SBX_MIXED_TENSOR, SBX_MIXED_WALSH = 0, 1
@@ -64,6 +67,7 @@ def load(path: str = LIB_PATH):
         "set_load": [vp, i32, vp, vp, vp, i32, vp, vp, vp],
         "set_initial": [vp, vp, vp, dbl, dbl],
         "step_n": [vp, i64, dbl, dbl],
+        "sbx_prepare_steps": [vp, i64, dbl, dbl],
         "sbx_get_step": [vp, C.POINTER(i64)],
         "sbx_set_step": [vp, i64],
         "read_field": [vp, i32, vp, i64],
@@ -83,6 +87,8 @@ def load(path: str = LIB_PATH):
         "sbx_read_history": [vp, vp, i64, C.POINTER(i64)],
         "sbx_lanczos": [vp, i64, vp, vp, vp],
         "sbx_set_mixed_kernel": [vp, i32],
+        "sbx_set_launch": [vp, i32, i32],
+        "sbx_get_launch": [vp, i32, C.POINTER(i32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -94,13 +100,20 @@ def load(path: str = LIB_PATH):
     return lib
 
 
+def _torch_dtype_name(a):
+    return str(a.dtype).replace("torch.", "")
+
+
 def _ptr(a, dtype=None):
-    """Raw pointer of a numpy array / torch tensor (None -> NULL)."""
+    """Raw pointer of a numpy array / torch tensor (None -> NULL); when
+    ``dtype`` is given, the element type must match it."""
     if a is None:
         return None
     if hasattr(a, "data_ptr"):
         if not a.is_contiguous():
             raise ValueError("tensor must be contiguous")
+        if dtype is not None and _torch_dtype_name(a) != np.dtype(dtype).name:
+            raise ValueError("expected dtype %s, got %s" % (np.dtype(dtype).name, a.dtype))
         return C.c_void_p(a.data_ptr())
     if not isinstance(a, np.ndarray) or not a.flags.c_contiguous:
         raise ValueError("expected a C-contiguous numpy array")
@@ -163,6 +176,10 @@ def set_initial(ctx, u0, v0, dt, alpha=0.0):
 
 def step_n(ctx, n_steps, dt, alpha=0.0):
     _check(ctx, load().step_n(ctx, int(n_steps), float(dt), float(alpha)))
+
+
+def sbx_prepare_steps(ctx, n_steps, dt, alpha=0.0):
+    _check(ctx, load().sbx_prepare_steps(ctx, int(n_steps), float(dt), float(alpha)))
 
 
 def set_modulus(ctx, E):
@@ -230,6 +247,16 @@ def sbx_lanczos(ctx, k, v0):
     return alpha, beta
 
 
+def sbx_set_launch(ctx, what, value):
+    _check(ctx, load().sbx_set_launch(ctx, int(what), int(value)))
+
+
+def sbx_get_launch(ctx, what) -> int:
+    v = C.c_int()
+    _check(ctx, load().sbx_get_launch(ctx, int(what), C.byref(v)))
+    return v.value
+
+
 def sbx_set_mixed_kernel(ctx, kind):
     _check(ctx, load().sbx_set_mixed_kernel(ctx, int(kind)))
 
@@ -263,14 +290,34 @@ def sbx_profile(ctx, n_steps, dt, alpha=0.0):
     return a.value, b.value
 
 
+def _device_array(a, name, dtype, numel):
+    if not (hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)):
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if a.numel() != numel:
+        raise ValueError("%s has %d entries, expected %d" % (name, a.numel(), numel))
+    return _ptr(a, dtype)
+
+
 def sbx_step_static(stream, n_dof, pat_nodes, pat_cells, K_packed, conn, sym, scale, minv, dt,
                     u_n, u_nm1):
     """One step that allocates nothing (device arrays in, u_nm1 overwritten
-    with U_{n+1}); pat_nodes / pat_cells are host arrays."""
+    with U_{n+1}); pat_nodes / pat_cells are host arrays.  The device arrays
+    are checked here for device, element type and length; the library
+    itself trusts their contents (node ids in [0, n_dof / 3), ops < 48)."""
+    pn = np.ascontiguousarray(pat_nodes, np.int32)
+    pc = np.ascontiguousarray(pat_cells, np.int64)
+    m = 3 * pn.astype(np.int64)
+    n_cells = int(pc.sum())
+    dev = [_device_array(K_packed, "K_packed", np.float64, int(np.sum(m * m))),
+           _device_array(conn, "conn", np.int32, int(np.sum(pn.astype(np.int64) * pc))),
+           _device_array(sym, "sym", np.uint8, n_cells),
+           _device_array(scale, "scale", np.float64, n_cells),
+           _device_array(minv, "minv", np.float64, int(n_dof)),
+           _device_array(u_n, "u_n", np.float64, int(n_dof)),
+           _device_array(u_nm1, "u_nm1", np.float64, int(n_dof))]
     rc = load().sbx_step_static(C.c_void_p(stream) if stream else None, int(n_dof),
-                                len(pat_nodes), _ptr(pat_nodes, np.int32), _ptr(pat_cells, np.int64),
-                                _ptr(K_packed), _ptr(conn), _ptr(sym), _ptr(scale), _ptr(minv),
-                                float(dt), _ptr(u_n), _ptr(u_nm1))
+                                len(pn), _ptr(pn, np.int32), _ptr(pc, np.int64),
+                                dev[0], dev[1], dev[2], dev[3], dev[4], float(dt), dev[5], dev[6])
     if rc != SBX_OK:
         raise SbxError(rc, "sbx_step_static failed")
 

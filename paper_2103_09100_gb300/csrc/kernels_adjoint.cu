@@ -15,9 +15,9 @@
 namespace sbx {
 namespace {
 
-int grid_for(int64_t n) {
-  int64_t g = (n + 255) / 256;
-  return (int)(g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g));
+int grid_for(const sbx_ctx *ctx, int64_t n) {
+  const int64_t g = (n + 255) / 256, cap = (int64_t)ctx->n_sm * 8;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
 __global__ void k_weight(int64_t nd, const double *w, const double *lam, double *v) {
@@ -127,13 +127,13 @@ size_t grad_smem(int m, bool fp32) {
 }  // namespace
 
 cudaError_t launch_weight(const sbx_ctx *ctx, const double *lam, double *v, cudaStream_t s) {
-  k_weight<<<grid_for(ctx->ndof), 256, 0, s>>>(ctx->ndof, ctx->d_w, lam, v);
+  k_weight<<<grid_for(ctx, ctx->ndof), 256, 0, s>>>(ctx->ndof, ctx->d_w, lam, v);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adj_update(const sbx_ctx *ctx, const double *f, const double *lam1,
                               double *lam2_to_lam, cudaStream_t s) {
-  k_adj_update<<<grid_for(ctx->ndof), 256, 0, s>>>(ctx->ndof, f, lam1, lam2_to_lam);
+  k_adj_update<<<grid_for(ctx, ctx->ndof), 256, 0, s>>>(ctx->ndof, f, lam1, lam2_to_lam);
   return cudaGetLastError();
 }
 
@@ -142,7 +142,7 @@ cudaError_t launch_residual(const sbx_ctx *ctx, int64_t n_rec, const int64_t *re
                             cudaStream_t s) {
   if (n_rec == 0) return cudaSuccess;
   (void)ctx;
-  k_residual<<<grid_for(n_rec), 256, 0, s>>>(n_rec, rec, u_n, data_n, lam, J);
+  k_residual<<<grid_for(ctx, n_rec), 256, 0, s>>>(n_rec, rec, u_n, data_n, lam, J);
   return cudaGetLastError();
 }
 

@@ -475,7 +475,7 @@ cudaError_t launch_update_batch(const sbx_ctx *ctx, const double *uc, double *up
   const int64_t nd = ctx->ndof * ctx->B;
   const double cm = 1.0 - 0.5 * alpha * dt, cp = 1.0 + 0.5 * alpha * dt;
   const int64_t want = (nd + 255) / 256;
-  const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), 152 * 8);
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)ctx->n_sm * 8);
   const double a = alpha == 0.0 ? 2.0 : 2.0 / cp, b = alpha == 0.0 ? 1.0 : cm / cp;
   float2 *pr = reinterpret_cast<float2 *>(pairs_out);
 #define SBX_UPD(D, F)                                                                          \

@@ -124,7 +124,7 @@ int lanczos_run(sbx_ctx *ctx, int64_t k, const double *v0_dev, double *alpha_dev
   const int64_t n = ctx->ndof;
   cudaStream_t s = ctx->stream;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + EIG_THREADS - 1) / EIG_THREADS,
-                                                               152 * 8));
+                                                               (int64_t)ctx->n_sm * 8));
   double *Q = nullptr, *a = nullptr, *t = nullptr, *f = nullptr, *w = nullptr, *part = nullptr,
          *h1 = nullptr, *h2 = nullptr, *nrm = nullptr;
   auto cleanup = [&]() {

@@ -298,10 +298,9 @@ __global__ void __launch_bounds__(256) k_update(int64_t nd, const double *__rest
   if (blockIdx.x == 0 && threadIdx.x == 0) *d_step += 1;
 }
 
-static int update_grid(int64_t nd) {
+static int update_grid(const sbx_ctx *ctx, int64_t nd) {
   int64_t want = (nd / 2 + 255) / 256;
-  int dev_sms = 152;
-  int64_t cap = (int64_t)dev_sms * 8;
+  int64_t cap = (int64_t)ctx->n_sm * 8;
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
@@ -318,6 +317,17 @@ __device__ __forceinline__ void put_pair(float *p, double x0, double x1, double 
   q[1] = make_float2(h2, l0);
   q[2] = make_float2(l1, l2);
 }
+// the same, written with an L2 eviction priority
+__device__ __forceinline__ void put_pair(float *p, double x0, double x1, double x2, uint64_t pol) {
+  float h0, h1, h2, l0, l1, l2;
+  split_f64(x0, h0, l0);
+  split_f64(x1, h1, l1);
+  split_f64(x2, h2, l2);
+  float2 *q = reinterpret_cast<float2 *>(p);
+  st_hint(q, make_float2(h0, h1), pol);
+  st_hint(q + 1, make_float2(h2, l0), pol);
+  st_hint(q + 2, make_float2(l1, l2), pol);
+}
 
 // UPD_U nodes per thread and round, all their loads issued before any
 // arithmetic (the update is bound by memory latency x parallelism).
@@ -330,6 +340,7 @@ __global__ void __launch_bounds__(256) k_update_f32(int64_t nn, const double *__
                                                     float *__restrict__ pairs, double a, double b,
                                                     int zero_f, int32_t *flags, int64_t *d_step) {
   bool bad = false;
+  const uint64_t stream = l2_evict_first(), keep = l2_evict_last();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < nn;
        i0 += UPD_U * stride) {
@@ -338,12 +349,12 @@ __global__ void __launch_bounds__(256) k_update_f32(int64_t nn, const double *__
 #pragma unroll
     for (int q = 0; q < UPD_U; ++q) {
       const int64_t i = i0 + q * stride < nn ? i0 + q * stride : i0;
-      fv[q] = f[i];
+      fv[q] = ld_hint(f + i, keep);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        wv[q][d] = w[3 * i + d];
-        cv[q][d] = uc[3 * i + d];
-        pv[q][d] = up[3 * i + d];
+        wv[q][d] = ld_nc_hint(w + 3 * i + d, stream);
+        cv[q][d] = ld_nc_hint(uc + 3 * i + d, stream);
+        pv[q][d] = ld_hint(up + 3 * i + d, stream);
       }
     }
 #pragma unroll
@@ -354,11 +365,11 @@ __global__ void __launch_bounds__(256) k_update_f32(int64_t nn, const double *__
       const double r1 = cdm_update<DAMPED>(wv[q][1], f2d_bits(fv[q].y), cv[q][1], pv[q][1], a, b);
       const double r2 = cdm_update<DAMPED>(wv[q][2], f2d_bits(fv[q].z), cv[q][2], pv[q][2], a, b);
       bad |= nonfinite(r0) || nonfinite(r1) || nonfinite(r2);
-      up[3 * i] = r0;
-      up[3 * i + 1] = r1;
-      up[3 * i + 2] = r2;
-      put_pair(pairs + 6 * i, r0, r1, r2);
-      if (zero_f) f[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      st_hint(up + 3 * i, r0, stream);
+      st_hint(up + 3 * i + 1, r1, stream);
+      st_hint(up + 3 * i + 2, r2, stream);
+      put_pair(pairs + 6 * i, r0, r1, r2, keep);
+      if (zero_f) st_hint(f + i, make_float4(0.0f, 0.0f, 0.0f, 0.0f), keep);
     }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 1);
@@ -410,7 +421,7 @@ __global__ void k_record(const int64_t *__restrict__ d_step, int64_t step0, int6
 
 cudaError_t launch_record(const sbx_ctx *ctx, const double *u, cudaStream_t s) {
   if (ctx->n_rec_hist == 0) return cudaSuccess;
-  const int grid = (int)std::min<int64_t>((ctx->n_rec_hist + 255) / 256, 152);
+  const int grid = (int)std::min<int64_t>((ctx->n_rec_hist + 255) / 256, ctx->n_sm);
   k_record<<<grid, 256, 0, s>>>(ctx->d_step, ctx->rec_step0, ctx->rec_cap, ctx->n_rec_hist,
                                 ctx->d_rec_idx, u, ctx->d_hist);
   return cudaGetLastError();
@@ -426,7 +437,7 @@ cudaError_t prepare_update(sbx_ctx *ctx, double dt, double alpha, cudaStream_t s
   if (ctx->w_valid && ctx->w_dt == dt && ctx->w_alpha == alpha) return cudaSuccess;
   const int64_t nd = ctx->ndof;   // w is per DOF, shared by all load cases
   const double cp = 1.0 + 0.5 * alpha * dt;
-  k_make_w<<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_minv, ctx->d_w, dt * dt / cp);
+  k_make_w<<<update_grid(ctx, nd), 256, 0, s>>>(nd, ctx->d_minv, ctx->d_w, dt * dt / cp);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     ctx->w_valid = true;
@@ -441,10 +452,10 @@ cudaError_t launch_update(const sbx_ctx *ctx, const double *uc, double *up, doub
   const int64_t nd = ctx->ndof * ctx->B;
   const double cm = 1.0 - 0.5 * alpha * dt, cp = 1.0 + 0.5 * alpha * dt;
   if (alpha == 0.0)
-    k_update<false><<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_w, f, uc, up, 2.0, 1.0, zero_f,
+    k_update<false><<<update_grid(ctx, nd), 256, 0, s>>>(nd, ctx->d_w, f, uc, up, 2.0, 1.0, zero_f,
                                                     ctx->d_flags, ctx->d_step);
   else
-    k_update<true><<<update_grid(nd), 256, 0, s>>>(nd, ctx->d_w, f, uc, up, 2.0 / cp, cm / cp,
+    k_update<true><<<update_grid(ctx, nd), 256, 0, s>>>(nd, ctx->d_w, f, uc, up, 2.0 / cp, cm / cp,
                                                    zero_f, ctx->d_flags, ctx->d_step);
   return cudaGetLastError();
 }
@@ -456,10 +467,10 @@ cudaError_t launch_update_f32(const sbx_ctx *ctx, const double *uc, double *up, 
   const double cm = 1.0 - 0.5 * alpha * dt, cp = 1.0 + 0.5 * alpha * dt;
   float4 *f = reinterpret_cast<float4 *>(f4);
   if (alpha == 0.0)
-    k_update_f32<false><<<update_grid(2 * nn), 256, 0, s>>>(
+    k_update_f32<false><<<update_grid(ctx, 2 * nn), 256, 0, s>>>(
         nn, ctx->d_w, f, uc, up, pairs_out, 2.0, 1.0, zero_f, ctx->d_flags, ctx->d_step);
   else
-    k_update_f32<true><<<update_grid(2 * nn), 256, 0, s>>>(
+    k_update_f32<true><<<update_grid(ctx, 2 * nn), 256, 0, s>>>(
         nn, ctx->d_w, f, uc, up, pairs_out, 2.0 / cp, cm / cp, zero_f, ctx->d_flags,
         ctx->d_step);
   return cudaGetLastError();
@@ -468,9 +479,9 @@ cudaError_t launch_update_f32(const sbx_ctx *ctx, const double *uc, double *up, 
 cudaError_t launch_split_pairs(const sbx_ctx *ctx, const double *u, float *pairs, cudaStream_t s) {
   if (ctx->B > 1) {
     const int64_t nv = ctx->ndof * ctx->B;
-    k_split_flat<<<update_grid(nv), 256, 0, s>>>(nv, u, reinterpret_cast<float2 *>(pairs));
+    k_split_flat<<<update_grid(ctx, nv), 256, 0, s>>>(nv, u, reinterpret_cast<float2 *>(pairs));
   } else {
-    k_split_pairs<<<update_grid(2 * ctx->N), 256, 0, s>>>(ctx->N, u, pairs);
+    k_split_pairs<<<update_grid(ctx, 2 * ctx->N), 256, 0, s>>>(ctx->N, u, pairs);
   }
   return cudaGetLastError();
 }
@@ -478,9 +489,9 @@ cudaError_t launch_split_pairs(const sbx_ctx *ctx, const double *u, float *pairs
 cudaError_t launch_widen_f32(const sbx_ctx *ctx, const float *f4, double *out, cudaStream_t s) {
   if (ctx->B > 1) {
     const int64_t nv = ctx->ndof * ctx->B;
-    k_widen_flat<<<update_grid(nv), 256, 0, s>>>(nv, f4, out);
+    k_widen_flat<<<update_grid(ctx, nv), 256, 0, s>>>(nv, f4, out);
   } else {
-    k_widen_f32<<<update_grid(2 * ctx->N), 256, 0, s>>>(
+    k_widen_f32<<<update_grid(ctx, 2 * ctx->N), 256, 0, s>>>(
         ctx->N, reinterpret_cast<const float4 *>(f4), out);
   }
   return cudaGetLastError();
@@ -509,7 +520,7 @@ __global__ void k_init_um1(int64_t nd, int B, const double *minv, const double *
 cudaError_t launch_init_um1(const sbx_ctx *ctx, const double *u0, const double *v0, double *um1,
                             const double *f, double dt, double alpha, cudaStream_t s) {
   const int64_t nd = ctx->ndof * ctx->B;
-  k_init_um1<<<update_grid(nd), 256, 0, s>>>(nd, ctx->B, ctx->d_minv, u0, v0, um1, f, dt, alpha);
+  k_init_um1<<<update_grid(ctx, nd), 256, 0, s>>>(nd, ctx->B, ctx->d_minv, u0, v0, um1, f, dt, alpha);
   return cudaGetLastError();
 }
 
@@ -521,7 +532,7 @@ __global__ void k_zero_fixed(int64_t nd, int B, const double *minv, double *u) {
 
 cudaError_t launch_zero_fixed(const sbx_ctx *ctx, double *u, cudaStream_t s) {
   const int64_t nd = ctx->ndof * ctx->B;
-  k_zero_fixed<<<update_grid(nd), 256, 0, s>>>(nd, ctx->B, ctx->d_minv, u);
+  k_zero_fixed<<<update_grid(ctx, nd), 256, 0, s>>>(nd, ctx->B, ctx->d_minv, u);
   return cudaGetLastError();
 }
 

@@ -7,8 +7,11 @@
 // Host code may not hand `g_static_force` itself to a kernel: in host code
 // that name is only a host-side stand-in for the device symbol.  The device
 // address is looked up once per device with cudaGetSymbolAddress (with that
-// device current) and cached; the first call on each device does this and
-// should therefore come before any stream capture.
+// device current) and cached, beside the device's SM count; the first call
+// on each device does this and should therefore come before any stream
+// capture.  The cache assumes the device's primary context lives as long as
+// the process: after a cudaDeviceReset the cached address is stale, and the
+// caller must not use this entry point again in that process.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -91,10 +94,17 @@ __global__ void k_update_static(int64_t nd, const double *minv, const double *f,
 
 std::mutex g_mu;
 double *g_addr[MAX_DEVICES] = {};   // device address of g_static_force, per device
+int g_sms[MAX_DEVICES] = {};        // multiprocessors of the device
 
-int scratch_address(int dev, double **out) {
+int scratch_address(int dev, double **out, int *sms) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_addr[dev]) {
+    int n_sm = 0;
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n_sm < 1) {
+      cudaGetLastError();
+      return SBX_ECUDA;
+    }
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_static_force) != cudaSuccess) {
       cudaGetLastError();
@@ -106,9 +116,11 @@ int scratch_address(int dev, double **out) {
       cudaGetLastError();
       return SBX_ECUDA;
     }
+    g_sms[dev] = n_sm;
     g_addr[dev] = static_cast<double *>(p);
   }
   *out = g_addr[dev];
+  *sms = g_sms[dev];
   return SBX_OK;
 }
 
@@ -150,7 +162,8 @@ extern "C" int sbx_step_static(void *cuda_stream, int64_t n_dof, int n_patterns,
     return SBX_ECUDA;
   }
   double *f = nullptr;
-  if (int rc = scratch_address(dev, &f)) return rc;
+  int n_sm = 0;
+  if (int rc = scratch_address(dev, &f, &n_sm)) return rc;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (cudaMemsetAsync(f, 0, (size_t)n_dof * sizeof(double), s) != cudaSuccess) {
     cudaGetLastError();
@@ -161,7 +174,7 @@ extern "C" int sbx_step_static(void *cuda_stream, int64_t n_dof, int n_patterns,
     k_force_static<<<(unsigned)tiles, 256, smem, s>>>(T, K_packed, conn, sym, scale, u_n, f);
   }
   int blocks = (int)((n_dof + 255) / 256);
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > n_sm * 8) blocks = n_sm * 8;
   k_update_static<<<blocks, 256, 0, s>>>(n_dof, minv, f, u_n, u_nm1, dt * dt);
   if (cudaGetLastError() != cudaSuccess) return SBX_ECUDA;
   return SBX_OK;

@@ -143,10 +143,15 @@ __device__ inline Stage stage_view(const unsigned char *base, uint32_t u_off) {
   return S;
 }
 
+// the FP32 force accumulator stays in L2 (evict_last) from the force
+// kernels to the update that reads and clears it
 __device__ __forceinline__ void red_add_v4(float *addr, float x, float y, float z) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(x), "f"(y),
-               "f"(z), "f"(0.0f)
-               : "memory");
+  asm volatile(
+      "{\n\t.reg .b64 pol;\n\t"
+      "createpolicy.fractional.L2::evict_last.b64 pol, 1.0;\n\t"
+      "red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, pol;\n\t}" ::"l"(addr),
+      "f"(x), "f"(y), "f"(z), "f"(0.0f)
+      : "memory");
 }
 
 // (hi - hi_ref) + (lo - lo_ref) per component; p, r: node pairs (hx hy hz lx ly lz)
@@ -786,6 +791,284 @@ __global__ void __launch_bounds__(GEN_THREADS) k_force_gen(const Tile *__restric
   }
 }
 
+// ------------------------------------ hanging-node patterns on the tensor cores
+// k_force_gen_tc: the cells of every pattern other than the identity-op
+// 8-node cell, in tiles of up to 128 cells of one pattern (any op), on the
+// 5th-generation tensor cores.  Persistent: CTA b takes tiles b, b + G, ...
+//  * the tile's record (one 1-D bulk copy, issued while the previous tile's
+//    MMAs and epilogue run): int32 {pat, ncell, n, 0}, float scale[128]
+//    (E_e h_e), uint8 sym[128], int32 ids[n][128] (node ids, master node
+//    order, slot-major);
+//  * B = K_p of the pattern as TF32 hi | lo, NP x KP each in the canonical
+//    no-swizzle K-major layout (NP = m rounded up to 16, KP = m rounded up
+//    to 8, zero padding), one bulk copy whenever the pattern changes;
+//  * A (128 x KP) = each cell's differences to its slot-0 node in the
+//    master frame (op applied), TF32 hi and lo, written to tensor memory by
+//    the threads (lane = cell; hi and lo interleaved every 8 columns);
+//  * D (tensor memory, 128 x NP) = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
+//    (tcgen05.mma kind::tf32, M128 N=NP K8, issued by one thread, completion
+//    by tcgen05.commit on an mbarrier);
+//  * epilogue: each cell's row of D (tcgen05.ld) times E_e h_e, back to the
+//    cell frame, one vector reduction per node.
+// Thread c = cell c of the tile; its nodes in groups of 8.
+constexpr int GT_THREADS = 128;
+constexpr int GT_GROUPS = 4;        // 8-node groups: up to 32 >= 26 nodes
+constexpr uint32_t GT_COLS = 256;   // TMEM: D in 0..79, A from column 80 on
+constexpr uint32_t GT_COL_A = 80;   // chunk ks: hi at 80 + 16 ks, lo at 88 + 16 ks
+constexpr int GT_NPMAX = 80, GT_KPMAX = 80;
+constexpr uint32_t GT_B_OFF = 128;
+constexpr uint32_t GT_REC_OFF = GT_B_OFF + 2u * GT_NPMAX * GT_KPMAX * 4u;
+
+__host__ __device__ inline int gt_kp(int m) { return (m + 7) & ~7; }
+__host__ __device__ inline int gt_np(int m) { return (m + 15) & ~15; }
+struct GtRec {
+  uint32_t scale, sym, ids, bytes;
+};
+__host__ __device__ inline GtRec gt_rec_layout(int n) {
+  GtRec R;
+  R.scale = 16;
+  R.sym = R.scale + 128u * 4u;
+  R.ids = R.sym + 128u;
+  R.bytes = R.ids + 128u * 4u * (uint32_t)n;
+  return R;
+}
+__host__ __device__ inline uint32_t gt_smem_bytes(int n_max) {
+  return GT_REC_OFF + gt_rec_layout(n_max).bytes;
+}
+
+__global__ void __launch_bounds__(GT_THREADS, 1)
+    k_force_gen_tc(const TcTile *__restrict__ tiles, int ntiles, const uint8_t *__restrict__ recs,
+                   const float *__restrict__ Bg, const int64_t *__restrict__ boff,
+                   const float *__restrict__ u, float *__restrict__ f4, LoadTable Ld,
+                   const int64_t *__restrict__ d_step, double dt, int32_t *flags) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [0] record, [1] B, [2] MMA
+  uint32_t *taddr_s = reinterpret_cast<uint32_t *>(smem + 32);
+  float *Bs = reinterpret_cast<float *>(smem + GT_B_OFF);
+  unsigned char *rec = smem + GT_REC_OFF;
+  const int tid = threadIdx.x, warp = tid >> 5, c = tid;
+  const int G = gridDim.x;
+  const uint32_t mb_rec = tc::smem_addr(&mbar[0]), mb_b = mb_rec + 8u, mb_mma = mb_rec + 16u;
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_addr(taddr_s), GT_COLS);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(mb_rec, 1);
+    tc::mbar_init(mb_b, 1);
+    tc::mbar_init(mb_mma, 1);
+    tc::mbar_fence_init();
+  }
+  if (blockIdx.x == 0 && Ld.n > 0) add_loads(Ld, d_step, dt, f4);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = *taddr_s;
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+
+  auto issue_record = [&](const TcTile &T) {   // thread 0
+    tc::fence_proxy_async_smem();
+    tc::mbar_arrive_expect_tx(mb_rec, (uint32_t)T.rec_bytes);
+    tc::bulk_g2s(tc::smem_addr(rec), recs + T.rec_off, (uint32_t)T.rec_bytes, mb_rec);
+  };
+  auto issue_b = [&](int pat) {   // thread 0
+    const int64_t o = boff[pat];
+    const uint32_t bytes = (uint32_t)(boff[pat + 1] - o) * 4u;
+    tc::fence_proxy_async_smem();
+    tc::mbar_arrive_expect_tx(mb_b, bytes);
+    tc::bulk_g2s(tc::smem_addr(Bs), Bg + o, bytes, mb_b);
+  };
+
+  uint32_t ph_rec = 0u, ph_b = 0u, ph_mma = 0u;
+  bool pend_rec = false, pend_b = false, pend_mma = false, ok = true;
+  int tile = blockIdx.x, bpat = -1;
+  if (tile < ntiles) {
+    const TcTile T = tiles[tile];
+    if (tid == 0) {
+      issue_record(T);
+      issue_b(T.pat);
+    }
+    pend_rec = pend_b = true;
+    bpat = T.pat;
+  }
+  for (; ok && tile < ntiles; tile += G) {
+    const int next = tile + G;
+    // this tile's record and B (issued during the previous tile)
+    bool got = tc::mbar_wait_bounded(mb_rec, ph_rec, WAIT_POLLS);
+    if (pend_b) got = tc::mbar_wait_bounded(mb_b, ph_b, WAIT_POLLS) && got;
+    ok = __syncthreads_and(got);
+    if (!ok) break;
+    ph_rec ^= 1u;
+    pend_rec = false;
+    if (pend_b) {
+      ph_b ^= 1u;
+      pend_b = false;
+    }
+    const int32_t *hdr = reinterpret_cast<const int32_t *>(rec);
+    const int ncell = hdr[1], n = hdr[2], m = 3 * n;
+    const int KP = gt_kp(m), NP = gt_np(m);
+    const GtRec R = gt_rec_layout(n);
+    const bool live = c < ncell;
+    const float sc = live ? reinterpret_cast<const float *>(rec + R.scale)[c] : 0.0f;
+    const int op = live ? (int)rec[R.sym + c] : 0;
+    const int32_t *ids = reinterpret_cast<const int32_t *>(rec + R.ids);
+    int32_t id[GT_GROUPS][8];
+    const int32_t id0 = live ? ids[c] : 0;
+#pragma unroll
+    for (int g = 0; g < GT_GROUPS; ++g)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int k = 8 * g + j;
+        id[g][j] = (live && k < n) ? ids[k * 128 + c] : -1;
+      }
+    int sg[3], pm[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      sg[r] = (op >> r) & 1;
+      pm[r] = op_perm_of(op, r);
+    }
+    __syncthreads();   // the record is read: its stage takes the next one
+    if (tid == 0 && next < ntiles) issue_record(tiles[next]);
+    pend_rec = next < ntiles;
+    // A: master-frame differences to slot 0, TF32 hi / lo, into TMEM
+    {
+      float ref[6];
+      if (live) {
+        const float2 a = *reinterpret_cast<const float2 *>(u + 6 * (int64_t)id0);
+        const float2 b = *reinterpret_cast<const float2 *>(u + 6 * (int64_t)id0 + 2);
+        const float2 d = *reinterpret_cast<const float2 *>(u + 6 * (int64_t)id0 + 4);
+        ref[0] = a.x; ref[1] = a.y; ref[2] = b.x; ref[3] = b.y; ref[4] = d.x; ref[5] = d.y;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) ref[q] = 0.0f;
+      }
+#pragma unroll
+      for (int g = 0; g < GT_GROUPS; ++g) {
+        if (24 * g >= KP) break;   // uniform over the CTA's tile
+        float p6[8][6];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (id[g][j] >= 0) {
+            const float *src = u + 6 * (int64_t)id[g][j];
+            const float2 a = *reinterpret_cast<const float2 *>(src);
+            const float2 b = *reinterpret_cast<const float2 *>(src + 2);
+            const float2 d = *reinterpret_cast<const float2 *>(src + 4);
+            p6[j][0] = a.x; p6[j][1] = a.y; p6[j][2] = b.x;
+            p6[j][3] = b.y; p6[j][4] = d.x; p6[j][5] = d.y;
+          } else {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) p6[j][q] = ref[q];
+          }
+        }
+        float hi[24], lo[24];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float d[3];
+#pragma unroll
+          for (int r = 0; r < 3; ++r) d[r] = (p6[j][r] - ref[r]) + (p6[j][3 + r] - ref[3 + r]);
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const float y = pm[r] == 0 ? d[0] : (pm[r] == 1 ? d[1] : d[2]);
+            const float x = sg[r] ? -y : y;
+            hi[3 * j + r] = tc::to_tf32(x);
+            lo[3 * j + r] = tc::to_tf32(x - hi[3 * j + r]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int ks = 3 * g + q;
+          if (8 * ks >= KP) break;
+          const float h8[8] = {hi[8 * q], hi[8 * q + 1], hi[8 * q + 2], hi[8 * q + 3],
+                               hi[8 * q + 4], hi[8 * q + 5], hi[8 * q + 6], hi[8 * q + 7]};
+          const float l8[8] = {lo[8 * q], lo[8 * q + 1], lo[8 * q + 2], lo[8 * q + 3],
+                               lo[8 * q + 4], lo[8 * q + 5], lo[8 * q + 6], lo[8 * q + 7]};
+          tc::tmem_st8(taddr + lane_base + GT_COL_A + 16u * (uint32_t)ks, h8);
+          tc::tmem_st8(taddr + lane_base + GT_COL_A + 16u * (uint32_t)ks + 8u, l8);
+        }
+      }
+      tc::tmem_st_wait();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      const uint32_t idesc = tc::idesc_tf32(128, NP);
+      const uint32_t b_hi = tc::smem_addr(Bs), b_lo = b_hi + (uint32_t)(NP * KP) * 4u;
+      const uint32_t sbo = (uint32_t)(KP / 4) * 128u;
+      for (int ks = 0; ks < KP / 8; ++ks) {
+        const uint32_t o = (uint32_t)ks * 256u;
+        const uint64_t bh = tc::smem_desc(b_hi + o, 128, sbo), bl = tc::smem_desc(b_lo + o, 128, sbo);
+        const uint32_t ah = taddr + GT_COL_A + 16u * (uint32_t)ks, al = ah + 8u;
+        tc::mma_tf32_ta(taddr, ah, bh, idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32_ta(taddr, ah, bl, idesc, 1u);
+        tc::mma_tf32_ta(taddr, al, bh, idesc, 1u);
+      }
+      tc::mma_commit(mb_mma);
+    }
+    pend_mma = true;
+    got = tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_POLLS);
+    ok = __syncthreads_and(got);
+    tc::fence_after_sync();
+    if (!ok) break;
+    ph_mma ^= 1u;
+    pend_mma = false;
+    // B of the next tile's pattern, if it differs (the MMAs reading B are done)
+    if (next < ntiles) {
+      const int np_ = tiles[next].pat;
+      if (np_ != bpat) {
+        if (tid == 0) issue_b(np_);
+        pend_b = true;
+        bpat = np_;
+      }
+    }
+    // epilogue: this cell's rows of D times E h, back to the cell frame
+#pragma unroll
+    for (int g = 0; g < GT_GROUPS; ++g) {
+      if (24 * g >= NP) break;
+      float v[24];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        float v8[8];
+        if (24 * g + 8 * q < NP) {
+          tc::tmem_ld8(taddr + lane_base + (uint32_t)(24 * g + 8 * q), v8);
+        } else {
+#pragma unroll
+          for (int z = 0; z < 8; ++z) v8[z] = 0.0f;
+        }
+#pragma unroll
+        for (int z = 0; z < 8; ++z) v[8 * q + z] = v8[z];
+      }
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (id[g][j] < 0) continue;
+        float y[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const float fv = sc * v[3 * j + r];
+          const float s = sg[r] ? -fv : fv;
+          y[0] += pm[r] == 0 ? s : 0.0f;
+          y[1] += pm[r] == 1 ? s : 0.0f;
+          y[2] += pm[r] == 2 ? s : 0.0f;
+        }
+        red_add_v4(f4 + 4 * (int64_t)id[g][j], y[0], y[1], y[2]);
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();   // D is read: the next tile's MMAs may overwrite it
+    tc::fence_after_sync();
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(flags, 2);
+    if (pend_rec) tc::mbar_wait_bounded(mb_rec, ph_rec, WAIT_POLLS);
+    if (pend_b) tc::mbar_wait_bounded(mb_b, ph_b, WAIT_POLLS);
+    if (pend_mma) tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_POLLS);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, GT_COLS);
+}
+
 // Self-test of the bounded completion wait every tensor-core kernel uses:
 // one thread waits on a fresh mbarrier (arrived on first when `arrive`),
 // giving up after `polls` polls; a give-up sets bit 2 of the flags, which
@@ -839,6 +1122,14 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   std::vector<int64_t> mark(ctx->N, -1);   // node -> last tile that holds it
   int64_t stamp = 0;
   ctx->n_brick_tiles = 0;
+  // k_force_gen_tc: per pattern B (TF32 hi | lo, canonical layout; offsets in
+  // floats, boff[P] = end) and 128-cell tile records
+  std::vector<float> Bgt;
+  std::vector<int64_t> boff(P + 1, 0);
+  std::vector<uint8_t> gt_recs;
+  std::vector<std::pair<int64_t, TcTile>> gt_tiles;   // (cost, tile)
+  std::vector<char> gt_has(P, 0);
+  int gt_nmax = 1;
   for (int p = 0; p < P; ++p) {
     if (cnt[p] == 0) continue;
     const int np = ctx->pat_nodes[p], m = 3 * np;
@@ -859,6 +1150,50 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
         gen.push_back(t);
       }
       gen_mmax = std::max(gen_mmax, m);
+      // tensor-core form: B_p, then records of up to 128 cells
+      {
+        const int KP = gt_kp(m), NP = gt_np(m), NKc = KP / 4;
+        boff[p] = (int64_t)Bgt.size();
+        gt_has[p] = 1;
+        Bgt.resize(Bgt.size() + 2 * (size_t)NP * KP, 0.0f);
+        float *Bh = Bgt.data() + boff[p], *Bl = Bh + (size_t)NP * KP;
+        for (int i = 0; i < m; ++i)
+          for (int j = 0; j < m; ++j) {
+            const double kv = ctx->K_host[ctx->pat_koff[p] + (int64_t)i * m + j];
+            const float hi = tf32_round_host((float)kv);
+            const float lo = tf32_round_host((float)(kv - (double)hi));
+            const size_t o = (size_t)(i >> 3) * NKc * 32 + (j >> 2) * 32 + (i & 7) * 4 + (j & 3);
+            Bh[o] = hi;
+            Bl[o] = lo;
+          }
+        gt_nmax = std::max(gt_nmax, np);
+        const GtRec R = gt_rec_layout(np);
+        const int64_t Cp = cnt[p];
+        for (int64_t c0 = 0; c0 < Cp; c0 += 128) {
+          const int nc = (int)std::min<int64_t>(128, Cp - c0);
+          const size_t at = gt_recs.size();
+          gt_recs.resize(at + R.bytes, 0);
+          const int32_t hdr[4] = {p, nc, np, 0};
+          put(gt_recs, at, hdr, 4);
+          std::vector<float> sc(128, 0.0f);
+          std::vector<uint8_t> sy(128, 0);
+          std::vector<int32_t> ids((size_t)np * 128, 0);
+          for (int c = 0; c < nc; ++c) {
+            sc[c] = (float)scale_sorted[start[p] + c0 + c];
+            sy[c] = sym_sorted[start[p] + c0 + c];
+            for (int k = 0; k < np; ++k)
+              ids[(size_t)k * 128 + c] = conn[conn_off[p] + (int64_t)k * Cp + c0 + c];
+          }
+          put(gt_recs, at + R.scale, sc.data(), 128);
+          put(gt_recs, at + R.sym, sy.data(), 128);
+          put(gt_recs, at + R.ids, ids.data(), ids.size());
+          TcTile t;
+          t.rec_off = (int64_t)at;
+          t.rec_bytes = (int32_t)R.bytes;
+          t.pat = p;
+          gt_tiles.emplace_back((int64_t)NP * KP * nc, t);
+        }
+      }
       continue;
     }
     // B = K_p hi | lo in the canonical layout (rows 24 .. 31 zero)
@@ -1033,6 +1368,24 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   if (int rc = up(&ctx->d_gen_tiles, gen)) return rc;
   if (int rc = up(&ctx->d_gen_K, Kpad)) return rc;
   if (int rc = up(&ctx->d_gen_koff, kpoff)) return rc;
+  {   // tensor-core form of the other patterns: heaviest tiles first;
+      // patterns without a B block get an empty range
+    boff[P] = (int64_t)Bgt.size();
+    for (int p = P - 1; p >= 0; --p)
+      if (!gt_has[p]) boff[p] = boff[p + 1];
+    std::stable_sort(gt_tiles.begin(), gt_tiles.end(),
+                     [](const std::pair<int64_t, TcTile> &a, const std::pair<int64_t, TcTile> &b) {
+                       return a.first > b.first;
+                     });
+    std::vector<TcTile> gtt;
+    for (auto &x : gt_tiles) gtt.push_back(x.second);
+    if (int rc = up(&ctx->d_gt_B, Bgt)) return rc;
+    if (int rc = up(&ctx->d_gt_boff, boff)) return rc;
+    if (int rc = up(&ctx->d_gt_rec, gt_recs)) return rc;
+    if (int rc = up(&ctx->d_gt_tiles, gtt)) return rc;
+    ctx->n_gt_tiles = (int)gtt.size();
+    ctx->gt_smem = gt_smem_bytes(gt_nmax);
+  }
   const int64_t nt = (int64_t)tiles.size();
   ctx->n_tc_tiles[0] = (int)nt;
   ctx->tc_rec_max[0] = recmax;
@@ -1040,8 +1393,7 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   ctx->tc_smem[0] = smem_layout(recmax, nnmax).total;
   ctx->n_gen_tiles = (int)gen.size();
   ctx->gen_smem = gen_smem(gen_mmax);
-  int nsm = 152;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int nsm = ctx->n_sm;
   // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per
   // CTA), at most 4 (registers, tensor memory); 3 when k_force_gen runs
   // beside it
@@ -1053,7 +1405,7 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   // 1-2 % slower on the cavity cube, k_force_gen filling in as they finish)
   ctx->wt_smem = wt_layout(recmax, nnmax).total;
   int per_sm_w = (int)((228u * 1024u) / (ctx->wt_smem + 1024u));
-  per_sm_w = std::max(1, std::min(per_sm_w, 6));
+  per_sm_w = std::max(1, std::min(per_sm_w, 8));
   ctx->wt_grid = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)nsm * per_sm_w));
   if (ctx->tc_smem[0] > 227u * 1024u) {
     err = "tensor-core tile needs more than 227 KB of shared memory";
@@ -1080,42 +1432,60 @@ cudaError_t prepare_tc_kernels() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_force_wht32, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_force_gen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)gt_smem_bytes(26));
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_force_gen, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)gen_smem(78));
 }
 
-// The two kernels run side by side: the tensor-core kernel's persistent
-// grid leaves room on every SM for one k_force_gen CTA, which runs on the
-// context's second stream (fork and join by events; also under capture).
+// The kernel of the regular cells and the kernel of the other patterns run
+// side by side: the second one on the context's second stream (fork and
+// join by events; also under capture), launched first.  Grids are sized so
+// that both are resident together: with k_force_gen_tc (one CTA and 256
+// TMEM columns per SM) the Walsh kernel takes 4 CTAs per SM (registers)
+// and the tcgen05 kernel of the regular cells 2 (tensor memory).
 cudaError_t launch_force_tc(const sbx_ctx *ctx, const float *pairs, float *f4, double dt,
                             cudaStream_t s) {
   LoadTable L = ctx->loads();   // added by CTA 0 of the first launch only
-  const bool both = ctx->n_tc_tiles[0] > 0 && ctx->n_gen_tiles > 0;
+  const bool gtc = ctx->hanging_tc && ctx->n_gt_tiles > 0;
+  const int n_hang = gtc ? ctx->n_gt_tiles : ctx->n_gen_tiles;
+  const bool both = ctx->n_tc_tiles[0] > 0 && n_hang > 0;
+  const int nsm = ctx->n_sm;
   cudaError_t e;
   if (both) {
     if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0)) != cudaSuccess) return e;
   }
-  if (ctx->n_tc_tiles[0] > 0 && ctx->mixed_wht && ctx->wht_pat >= 0) {
-    WhtF kw;
-    for (int q = 0; q < 72; ++q) kw.blk[q] = (float)(ctx->wht.blk[q] * 0.125);
-    k_force_wht32<<<ctx->wt_grid, WT_THREADS, ctx->wt_smem, s>>>(
-        ctx->d_tc_tiles[0], ctx->n_tc_tiles[0], ctx->d_tc_rec, kw, pairs, f4, L, ctx->d_step, dt,
-        ctx->d_flags, ctx->tc_rec_max[0], ctx->tc_nn_max[0]);
-    L.n = 0;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  } else if (ctx->n_tc_tiles[0] > 0) {
-    k_force_tc<<<ctx->tc_grid[0], TC_THREADS, ctx->tc_smem[0], s>>>(
-        ctx->d_tc_tiles[0], ctx->n_tc_tiles[0], ctx->d_tc_rec, ctx->d_tc_K, pairs, f4, L,
-        ctx->d_step, dt, ctx->d_flags, ctx->tc_rec_max[0], ctx->tc_nn_max[0]);
+  if (n_hang > 0) {
+    cudaStream_t sg = both ? ctx->side : s;
+    if (gtc) {
+      const int grid = std::min(ctx->n_gt_tiles, nsm);
+      k_force_gen_tc<<<grid, GT_THREADS, ctx->gt_smem, sg>>>(
+          ctx->d_gt_tiles, ctx->n_gt_tiles, ctx->d_gt_rec, ctx->d_gt_B, ctx->d_gt_boff, pairs, f4,
+          L, ctx->d_step, dt, ctx->d_flags);
+    } else {
+      k_force_gen<<<ctx->n_gen_tiles, GEN_THREADS, ctx->gen_smem, sg>>>(
+          ctx->d_gen_tiles, ctx->view(), ctx->d_gen_K, ctx->d_gen_koff, pairs, f4, L, ctx->d_step,
+          dt);
+    }
     L.n = 0;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (ctx->n_gen_tiles > 0) {
-    cudaStream_t sg = both ? ctx->side : s;
-    k_force_gen<<<ctx->n_gen_tiles, GEN_THREADS, ctx->gen_smem, sg>>>(ctx->d_gen_tiles, ctx->view(),
-                                                              ctx->d_gen_K, ctx->d_gen_koff,
-                                                              pairs, f4, L, ctx->d_step, dt);
+  if (ctx->n_tc_tiles[0] > 0 && ctx->mixed_wht && ctx->wht_pat >= 0) {
+    WhtF kw;
+    for (int q = 0; q < 72; ++q) kw.blk[q] = (float)(ctx->wht.blk[q] * 0.125);
+    const int per_sm = ctx->walsh_ctas > 0 ? ctx->walsh_ctas : (gtc ? 4 : 6);
+    const int grid = std::max(1, std::min(ctx->wt_grid, per_sm * nsm));
+    k_force_wht32<<<grid, WT_THREADS, ctx->wt_smem, s>>>(
+        ctx->d_tc_tiles[0], ctx->n_tc_tiles[0], ctx->d_tc_rec, kw, pairs, f4, L, ctx->d_step, dt,
+        ctx->d_flags, ctx->tc_rec_max[0], ctx->tc_nn_max[0]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if (ctx->n_tc_tiles[0] > 0) {
+    const int grid = gtc ? std::max(1, std::min(ctx->tc_grid[0], 2 * nsm)) : ctx->tc_grid[0];
+    k_force_tc<<<grid, TC_THREADS, ctx->tc_smem[0], s>>>(
+        ctx->d_tc_tiles[0], ctx->n_tc_tiles[0], ctx->d_tc_rec, ctx->d_tc_K, pairs, f4, L,
+        ctx->d_step, dt, ctx->d_flags, ctx->tc_rec_max[0], ctx->tc_nn_max[0]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (both) {

@@ -101,6 +101,10 @@ void drop_graph(sbx_ctx *ctx) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  for (auto &kv : ctx->graph.tail)
+    for (auto &g : kv.second)
+      if (g) cudaGraphExecDestroy(g);
+  ctx->graph.tail.clear();
   ctx->graph.valid = false;
 }
 
@@ -111,8 +115,8 @@ void free_mesh(sbx_ctx *ctx) {
   dfree(ctx->d_w);
   ctx->w_valid = false;
   dfree(ctx->d_u[0]); dfree(ctx->d_u[1]); dfree(ctx->d_f); dfree(ctx->d_fx);
-  dfree(ctx->d_pair[0]); dfree(ctx->d_pair[1]);
-  ctx->pair_valid[0] = ctx->pair_valid[1] = false;
+  dfree(ctx->d_pair);
+  ctx->pair_of = -1;
   dfree(ctx->d_tiles_simt);
   dfree(ctx->d_tiles_rest);
   ctx->n_tiles_rest = 0;
@@ -121,6 +125,8 @@ void free_mesh(sbx_ctx *ctx) {
   dfree(ctx->d_load_dof); dfree(ctx->d_load_amp); dfree(ctx->d_load_t1); dfree(ctx->d_load_ncyc);
   dfree(ctx->d_load_kind);
   dfree(ctx->d_tc_K); dfree(ctx->d_tc_rec); dfree(ctx->d_gen_tiles); dfree(ctx->d_gen_K);
+  dfree(ctx->d_gt_rec); dfree(ctx->d_gt_tiles); dfree(ctx->d_gt_B); dfree(ctx->d_gt_boff);
+  ctx->n_gt_tiles = 0;
   dfree(ctx->d_gen_koff);
   dfree(ctx->d_rec_idx); dfree(ctx->d_hist);
   ctx->n_rec_hist = ctx->rec_cap = 0;
@@ -153,11 +159,11 @@ int force(sbx_ctx *ctx, const double *u, double *f, double dt) {
   if (ctx->uses_pairs()) {
     const int p = u == ctx->d_u[0] ? 0 : (u == ctx->d_u[1] ? 1 : -1);
     if (p < 0) return fail(ctx, SBX_EINVAL, "this form's force runs on the state buffers only");
-    if (!ctx->pair_valid[p]) {
-      CK(sbx::launch_split_pairs(ctx, u, ctx->d_pair[p], ctx->stream));
-      ctx->pair_valid[p] = true;
+    if (ctx->pair_of != p) {
+      CK(sbx::launch_split_pairs(ctx, u, ctx->d_pair, ctx->stream));
+      ctx->pair_of = p;
     }
-    pairs = ctx->d_pair[p];
+    pairs = ctx->d_pair;
   }
   if (ctx->B > 1) {
     CK(sbx::launch_force_batch(ctx, pairs ? (const void *)pairs : (const void *)u, f, dt,
@@ -173,14 +179,14 @@ int force(sbx_ctx *ctx, const double *u, double *f, double dt) {
 int update(sbx_ctx *ctx, const double *uc, double *up, double dt, double alpha, int zero_f) {
   if (ctx->B > 1) {
     const int p = up == ctx->d_u[0] ? 0 : 1;
-    float *pairs_out = ctx->uses_pairs() ? ctx->d_pair[p] : nullptr;
+    float *pairs_out = ctx->uses_pairs() ? ctx->d_pair : nullptr;
     CK(sbx::launch_update_batch(ctx, uc, up, ctx->d_f, pairs_out, dt, alpha, zero_f, ctx->stream));
-    if (pairs_out) ctx->pair_valid[p] = true;
+    if (pairs_out) ctx->pair_of = p;
   } else if (ctx->prec == SBX_PREC_MIXED) {
     const int p = up == ctx->d_u[0] ? 0 : 1;
-    CK(sbx::launch_update_f32(ctx, uc, up, reinterpret_cast<float *>(ctx->d_f), ctx->d_pair[p], dt,
+    CK(sbx::launch_update_f32(ctx, uc, up, reinterpret_cast<float *>(ctx->d_f), ctx->d_pair, dt,
                               alpha, zero_f, ctx->stream));
-    ctx->pair_valid[p] = true;
+    ctx->pair_of = p;
   } else {
     CK(sbx::launch_update(ctx, uc, up, ctx->d_f, dt, alpha, zero_f, ctx->stream));
   }
@@ -190,9 +196,9 @@ int update(sbx_ctx *ctx, const double *uc, double *up, double dt, double alpha, 
 // Mixed form: make the (hi, lo) pairs of U_n current before replaying a
 // graph (the captured steps take them from the previous update).
 int ensure_pairs(sbx_ctx *ctx) {
-  if (!ctx->uses_pairs() || ctx->pair_valid[ctx->cur]) return SBX_OK;
-  CK(sbx::launch_split_pairs(ctx, ctx->d_u[ctx->cur], ctx->d_pair[ctx->cur], ctx->stream));
-  ctx->pair_valid[ctx->cur] = true;
+  if (!ctx->uses_pairs() || ctx->pair_of == ctx->cur) return SBX_OK;
+  CK(sbx::launch_split_pairs(ctx, ctx->d_u[ctx->cur], ctx->d_pair, ctx->stream));
+  ctx->pair_of = ctx->cur;
   return SBX_OK;
 }
 
@@ -210,12 +216,17 @@ constexpr int GRAPH_UNIT = 32;  // steps per replayed graph (even)
 
 int build_graphs(sbx_ctx *ctx, double dt, double alpha) {
   drop_graph(ctx);
+  const int pair_before = ctx->pair_of;
   for (int parity = 0; parity < 2; ++parity) {
     cudaGraph_t g;
+    // a graph is replayed with the pairs of its first U_n current
+    // (ensure_pairs), so no split is captured into it
+    ctx->pair_of = parity;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     int rc = SBX_OK;
     for (int s = 0; s < GRAPH_UNIT && rc == SBX_OK; ++s) rc = one_step(ctx, parity ^ (s & 1), dt, alpha, 1);
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    ctx->pair_of = pair_before;
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(&ctx->graph.exec[parity], g, 0);
@@ -226,6 +237,39 @@ int build_graphs(sbx_ctx *ctx, double dt, double alpha) {
   ctx->graph.dt = dt;
   ctx->graph.alpha = alpha;
   ctx->graph.unit = GRAPH_UNIT;
+  return SBX_OK;
+}
+
+// The graphs of a call's last r + 1 steps (r < GRAPH_UNIT full steps, then
+// the closing step that keeps R_int), for both parities of the state pair.
+int build_tail(sbx_ctx *ctx, int r, double dt, double alpha) {
+  if (!ctx->graph.valid || ctx->graph.dt != dt || ctx->graph.alpha != alpha)
+    if (int rc = build_graphs(ctx, dt, alpha)) return rc;
+  if (ctx->graph.tail.count(r)) return SBX_OK;
+  std::array<cudaGraphExec_t, 2> ex = {nullptr, nullptr};
+  const int pair_before = ctx->pair_of;
+  for (int parity = 0; parity < 2; ++parity) {
+    cudaGraph_t g;
+    ctx->pair_of = parity;   // as in build_graphs
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = SBX_OK;
+    for (int s = 0; s <= r && rc == SBX_OK; ++s)
+      rc = one_step(ctx, parity ^ (s & 1), dt, alpha, s < r ? 1 : 0);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    ctx->pair_of = pair_before;
+    if (rc == SBX_OK && e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaStreamEndCapture");
+    if (rc == SBX_OK) {
+      e = cudaGraphInstantiate(&ex[parity], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    if (rc) {
+      for (auto &x : ex)
+        if (x) cudaGraphExecDestroy(x);
+      return rc;
+    }
+  }
+  ctx->graph.tail[r] = ex;
   return SBX_OK;
 }
 
@@ -253,7 +297,10 @@ int sbx_create(sbx_ctx **out, int device, void *cuda_stream) {
   sbx_ctx *ctx = new (std::nothrow) sbx_ctx();
   if (!ctx) return SBX_ENOMEM;
   ctx->device = device;
-  if (cudaSetDevice(device) != cudaSuccess) {
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      ctx->n_sm < 1) {
+    cudaGetLastError();
     delete ctx;
     return SBX_ECUDA;
   }
@@ -539,8 +586,7 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   const bool pairs = (precision_mode == SBX_PREC_MIXED && n_rhs == 1) ||
                      (precision_mode == SBX_PREC_FP32 && n_rhs > 1);
   if (!rc && pairs) rc = dalloc(ctx, &ctx->d_fx, nfield);
-  if (!rc && pairs) rc = dalloc(ctx, &ctx->d_pair[0], 2 * nfield);
-  if (!rc && pairs) rc = dalloc(ctx, &ctx->d_pair[1], 2 * nfield);
+  if (!rc && pairs) rc = dalloc(ctx, &ctx->d_pair, 2 * nfield);
   if (rc) {
     free_mesh(ctx);
     return rc;
@@ -662,7 +708,7 @@ int set_initial(sbx_ctx *ctx, const double *u0, const double *v0, double dt, dou
   const int64_t nd = ctx->ndof * ctx->B;
   const size_t bytes = nd * sizeof(double);
   ctx->cur = 0;
-  ctx->pair_valid[0] = ctx->pair_valid[1] = false;
+  ctx->pair_of = -1;
   double *U0 = ctx->d_u[0], *Um1 = ctx->d_u[1];
   if (u0) {
     CK(cudaMemcpyAsync(U0, u0, bytes, cudaMemcpyDefault, ctx->stream));
@@ -711,24 +757,36 @@ int step_n(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha) {
   CK(sbx::prepare_update(ctx, dt, alpha, ctx->stream));
   if (int rc = ensure_pairs(ctx)) return rc;
   int64_t left = n_steps - 1;  // the last step keeps R_int for read-back
-  if (left >= GRAPH_UNIT) {
-    if (!ctx->graph.valid || ctx->graph.dt != dt || ctx->graph.alpha != alpha)
-      if (int rc = build_graphs(ctx, dt, alpha)) return rc;
+  if (!ctx->graph.valid || ctx->graph.dt != dt || ctx->graph.alpha != alpha)
+    if (int rc = build_graphs(ctx, dt, alpha)) return rc;
+  {
     while (left >= GRAPH_UNIT) {
       CK(cudaGraphLaunch(ctx->graph.exec[ctx->cur], ctx->stream));
       left -= GRAPH_UNIT;
     }
   }
-  while (left > 0) {
-    if (int rc = one_step(ctx, ctx->cur, dt, alpha, 1)) return rc;
-    ctx->cur ^= 1;
-    --left;
-  }
-  if (int rc = one_step(ctx, ctx->cur, dt, alpha, 0)) return rc;
-  ctx->cur ^= 1;
+  // the remaining left steps and the closing one, as one graph
+  if (int rc = build_tail(ctx, (int)left, dt, alpha)) return rc;
+  if (int rc = ensure_pairs(ctx)) return rc;
+  CK(cudaGraphLaunch(ctx->graph.tail[(int)left][ctx->cur], ctx->stream));
+  ctx->cur ^= (int)((left + 1) & 1);
+  // the last update wrote the pairs of the new U_n
+  if (ctx->uses_pairs()) ctx->pair_of = ctx->cur;
   ctx->f_dirty = true;
   ctx->step += n_steps;
   return SBX_OK;
+}
+
+int sbx_prepare_steps(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before sbx_prepare_steps");
+  if (n_steps < 0 || !(dt > 0) || !(alpha >= 0) || !isfinite(dt) || !isfinite(alpha))
+    return fail(ctx, SBX_EINVAL, "need n_steps >= 0, dt > 0, alpha >= 0");
+  if (n_steps == 0) return SBX_OK;
+  CK(sbx::prepare_update(ctx, dt, alpha, ctx->stream));
+  return build_tail(ctx, (int)((n_steps - 1) % GRAPH_UNIT), dt, alpha);
 }
 
 int sbx_profile(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha, double *ms_force,
@@ -998,7 +1056,7 @@ int sbx_wait_selftest(sbx_ctx *ctx, int64_t polls, int arrive) {
 
 int sbx_touch(sbx_ctx *ctx) {
   if (!ctx) return SBX_EINVAL;
-  ctx->pair_valid[0] = ctx->pair_valid[1] = false;
+  ctx->pair_of = -1;
   return SBX_OK;
 }
 
@@ -1052,6 +1110,40 @@ int sbx_set_mixed_kernel(sbx_ctx *ctx, int kind) {
   if (ctx->mixed_wht != w) drop_graph(ctx);
   ctx->mixed_wht = w;
   return SBX_OK;
+}
+
+int sbx_set_launch(sbx_ctx *ctx, int what, int value) {
+  if (!ctx) return SBX_EINVAL;
+  ctx->err.clear();
+  switch (what) {
+    case SBX_LAUNCH_HANGING_KERNEL:
+      if (value != SBX_HANGING_SIMT && value != SBX_HANGING_TENSOR)
+        return fail(ctx, SBX_EINVAL, "unknown kernel for the hanging-node patterns");
+      if (ctx->hanging_tc != (value == SBX_HANGING_TENSOR)) drop_graph(ctx);
+      ctx->hanging_tc = value == SBX_HANGING_TENSOR;
+      return SBX_OK;
+    case SBX_LAUNCH_WALSH_CTAS_PER_SM:
+      if (value < 0 || value > 8) return fail(ctx, SBX_EINVAL, "Walsh-kernel CTAs per SM: 0 .. 8");
+      if (ctx->walsh_ctas != value) drop_graph(ctx);
+      ctx->walsh_ctas = value;
+      return SBX_OK;
+    default:
+      return fail(ctx, SBX_EINVAL, "unknown launch parameter");
+  }
+}
+
+int sbx_get_launch(sbx_ctx *ctx, int what, int *value) {
+  if (!ctx || !value) return SBX_EINVAL;
+  switch (what) {
+    case SBX_LAUNCH_HANGING_KERNEL:
+      *value = ctx->hanging_tc ? SBX_HANGING_TENSOR : SBX_HANGING_SIMT;
+      return SBX_OK;
+    case SBX_LAUNCH_WALSH_CTAS_PER_SM:
+      *value = ctx->walsh_ctas;
+      return SBX_OK;
+    default:
+      return fail(ctx, SBX_EINVAL, "unknown launch parameter");
+  }
 }
 
 int sbx_set_receivers(sbx_ctx *ctx, int64_t n_rec, const int64_t *rec_idx, int64_t max_steps) {
@@ -1205,7 +1297,7 @@ int write_field(sbx_ctx *ctx, int which, const double *in, int64_t len) {
   else
     return fail(ctx, SBX_EINVAL, "only U_N and U_NM1 can be written");
   CK(cudaMemcpyAsync(dst, in, len * sizeof(double), cudaMemcpyDefault, ctx->stream));
-  ctx->pair_valid[dst == ctx->d_u[0] ? 0 : 1] = false;
+  if (ctx->pair_of == (dst == ctx->d_u[0] ? 0 : 1)) ctx->pair_of = -1;
   return SBX_OK;
 }
 

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -66,12 +68,16 @@ struct GraphCache {
   double dt = 0, alpha = 0;
   int unit = 0;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  // tail[r][parity]: r full steps then the closing step (which keeps
+  // R_int), for the r = (n_steps - 1) mod unit steps a call has left over
+  std::map<int, std::array<cudaGraphExec_t, 2>> tail;
 };
 
 }  // namespace sbx
 
 struct sbx_ctx {
   int device = 0;
+  int n_sm = 1;                    // multiprocessors of the device (grid sizing)
   cudaStream_t stream = nullptr;
   // second stream for a force kernel that runs beside the first (forked
   // from and joined back into `stream` with the two events)
@@ -111,10 +117,14 @@ struct sbx_ctx {
   int cur = 0;                     // d_u[cur] = U_n, d_u[cur ^ 1] = U_{n-1}
   double *d_f = nullptr;           // R_int - R_ext accumulator; SBX_PREC_MIXED: float [N][4]
   double *d_fx = nullptr;          // SBX_PREC_MIXED: d_f widened to FP64 [3N] on demand
-  // SBX_PREC_MIXED: d_u[p] split into FP32 (hi xyz, lo xyz) per node, written
-  // by the update kernel (or by k_split_pairs after a host write)
-  float *d_pair[2] = {nullptr, nullptr};
-  bool pair_valid[2] = {false, false};
+  // SBX_PREC_MIXED (and batched FP32): one state buffer split into FP32
+  // (hi xyz, lo xyz) per node, written by the update kernel (or by
+  // k_split_pairs after a host write).  One buffer serves both state
+  // buffers: the update of step n writes the pairs of U_{n+1} over those of
+  // U_n, which the force of step n has finished reading.  pair_of = the
+  // state buffer (0, 1) whose pairs it holds, -1 for none.
+  float *d_pair = nullptr;
+  int pair_of = -1;
   bool f_dirty = false;
   bool f_pending = false;          // sbx_force done, sbx_update not yet
   std::vector<int64_t> h_fixed;    // Dirichlet DOFs (M^-1 = 0)
@@ -147,6 +157,16 @@ struct sbx_ctx {
   int64_t *d_gen_koff = nullptr;
   int n_gen_tiles = 0;
   size_t gen_smem = 0;
+  // the other patterns on the tensor cores (k_force_gen_tc): 128-cell tile
+  // records, per-pattern B = K_p TF32 hi | lo (offsets in floats, P + 1)
+  uint8_t *d_gt_rec = nullptr;
+  sbx::TcTile *d_gt_tiles = nullptr;
+  float *d_gt_B = nullptr;
+  int64_t *d_gt_boff = nullptr;
+  int n_gt_tiles = 0;
+  size_t gt_smem = 0;
+  bool hanging_tc = false;         // k_force_gen_tc instead of k_force_gen
+  int walsh_ctas = 0;              // Walsh-kernel CTAs per SM (0: automatic)
   // the 8-node tiles by the Walsh-basis SIMT kernel instead of the tensor
   // cores (sbx_set_mixed_kernel)
   bool mixed_wht = false;

@@ -2,13 +2,17 @@
 not call cudaMalloc: e.g. code running while a framework's caching
 allocator owns the device, or real-time loops where an allocation could
 stall or fail.  Its result must match the ordinary context-based step_n
-on two consecutive calls.  This file is collected last on purpose.
+on two consecutive calls, and the FP64 oracle's step.  The file name sorts
+last, so pytest collects it last: a run that stops at its first failure has
+then already run every other test before this one.
 """
 import numpy as np
 import pytest
 
 import octree_gen as og
+from oracle import cdm
 from paper_2103_09100_gb300 import Solver, _lib as L, build, patterns
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -68,16 +72,29 @@ def test_static_step_matches_step_n_twice():
     torch.cuda.synchronize()
     got2 = u0.cpu().numpy()
     S.close()
-    rel = lambda x, y: np.linalg.norm(x - y) / np.linalg.norm(y)
     assert rel(got1, ref1) < 1e-12
     assert rel(got2, ref2) < 1e-12
+    # and the oracle's two undamped, unloaded steps from the same pair
+    P = cdm.make_problem(m, dt=S.dt)
+    o1, o0, _, _ = cdm.run(P, 1, a, b)
+    o2, _, _, _ = cdm.run(P, 1, o1, o0, n0=1)
+    assert rel(got1, o1) < 1e-12
+    assert rel(got2, o2) < 1e-12
+    # the wrapper refuses host arrays and wrong element types
+    with pytest.raises(ValueError):
+        L.sbx_step_static(stream, nd, nn, counts, K, conn, sym, scale, minv, S.dt, u1, u0)
+    with pytest.raises(ValueError):
+        L.sbx_step_static(stream, nd, nn, counts, K, conn.long(), sym, scale, d_minv, S.dt, u1, u0)
 
 
 def test_static_step_rejects_oversized_problem():
     torch = pytest.importorskip("torch")
     build.build()
+    import ctypes as C
     x = torch.zeros(3, dtype=torch.float64, device="cuda")
-    with pytest.raises(L.SbxError) as e:
-        L.sbx_step_static(None, L.SBX_STATIC_MAX_DOF + 3, np.array([8], np.int32),
-                          np.array([1], np.int64), x, x, x, x, x, 1e-3, x, x)
-    assert e.value.code == L.SBX_EINVAL
+    p = C.c_void_p(x.data_ptr())
+    nn = np.array([8], np.int32)
+    cells = np.array([1], np.int64)
+    rc = L.load().sbx_step_static(None, L.SBX_STATIC_MAX_DOF + 3, 1, nn.ctypes.data_as(C.c_void_p),
+                                  cells.ctypes.data_as(C.c_void_p), p, p, p, p, p, 1e-3, p, p)
+    assert rc == L.SBX_EINVAL
