@@ -13,7 +13,9 @@ term, lumped-mass central-difference update.  Three forms are measured:
   history) on the multi-point octree (levels 3-7, ~200k cells); its unit is
   DOF·load-case·steps/s;
 * ``forms.trench_mixed``: the mixed form on the layered-trench octree
-  (levels 5-10, ~9.5M cells, ~32M DOF), 500 steps, with its device memory;
+  (levels 5-10, a trench of finite length and curved layer interfaces,
+  ~7.7M cells, ~30M DOF, 42 patterns), 500 steps, with its device memory
+  and its error against the FP64 form;
 * ``forms.lanczos_cube``: 300 steps of the GPU Lanczos iteration for the
   eigenfrequencies of a roller-supported 64^3 cube (~824k DOF), with the
   lowest Ritz frequency against the continuum one.
@@ -324,12 +326,17 @@ def run_batched_only(args):
     stream = torch.cuda.Stream()
     S = Solver.from_mesh(mb, precision="fp32", n_rhs=B, stream=stream.cuda_stream)
     S.initial()
+    from paper_2103_09100_gb300 import autotune
+    tuned = autotune.tune(S, steps=5, repeats=3)
+    S.initial()
     S.step(args.warmup)
+    L.sbx_prepare_steps(S.ctx, args.only_batched, S.dt, S.alpha)
     ms = time_steps(S, stream, args.only_batched, 1, torch)
     ms_f, ms_u = L.sbx_profile(S.ctx, 20, S.dt, S.alpha)
     print(json.dumps({"form": "batched", "value": mb.n_dof * B * args.only_batched / (ms * 1e-3),
                       "unit": "DOF*load_cases*steps/s", "ms_per_step": ms / args.only_batched,
                       "force_ms": ms_f / 20, "update_ms": ms_u / 20,
+                      "autotune": {str(k): v for k, v in tuned["params"].items()},
                       "workload": "%s (%d cells, %d DOF), B = %d" % (mb.name, mb.n_cells, mb.n_dof, B)}),
           flush=True)
     S.close()
@@ -347,9 +354,9 @@ def main():
     ap.add_argument("--mixed-kernel", default="walsh", choices=["walsh", "tensor"],
                     help="mixed form: kernel for the regular 8-node cells of the headline "
                          "solver (walsh: Walsh-basis FP32 SIMT, the default; tensor: tcgen05)")
-    ap.add_argument("--hanging", default="simt", choices=["simt", "tensor"],
-                    help="mixed form: kernel for the hanging-node patterns (simt: FP32 FFMA; "
-                         "tensor: tcgen05, TF32x3)")
+    ap.add_argument("--hanging", default=None, choices=["simt", "tensor"],
+                    help="mixed form: kernel for the hanging-node patterns (tensor: tcgen05, "
+                         "TF32x3, the library's default; simt: FP32 FFMA)")
     ap.add_argument("--walsh-ctas", type=int, default=0,
                     help="mixed form: Walsh-kernel CTAs per SM (0: the library's choice)")
     ap.add_argument("--e2e-steps", type=int, default=2000)
@@ -387,10 +394,13 @@ def main():
     S = Solver.from_mesh(mesh, precision=args.precision, device=local, stream=stream.cuda_stream)
     if args.precision == "mixed" and args.mixed_kernel == "tensor":
         L.sbx_set_mixed_kernel(S.ctx, L.SBX_MIXED_TENSOR)
-    if args.precision == "mixed":
+    if args.precision == "mixed" and args.hanging is not None:
         L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_HANGING_KERNEL,
                          L.SBX_HANGING_TENSOR if args.hanging == "tensor" else L.SBX_HANGING_SIMT)
+    if args.precision == "mixed":
         L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_WALSH_CTAS_PER_SM, args.walsh_ctas)
+    hanging_tc = (args.precision == "mixed" and
+                  L.sbx_get_launch(S.ctx, L.SBX_LAUNCH_HANGING_KERNEL) == L.SBX_HANGING_TENSOR)
     S.initial()
     S.step(args.warmup)
     # the graphs step_n(steps) replays are built before the timed region
@@ -427,11 +437,14 @@ def main():
         mixed = args.precision == "mixed"
         roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"],
-                "traffic": measured_traffic("mixed_walsh_pair" if walsh_cells else "mixed_tensor_pair")
+                "traffic": measured_traffic(("mixed_walsh" if walsh_cells else "mixed_tensor") +
+                                            ("_gen_tc_pair" if hanging_tc else "_gen_simt_pair"))
                 if mixed else None,
-                "kernel": ("force launch pair k_force_wht32 (8-node cells, Walsh basis) + "
-                           "k_force_gen (concurrent streams)" if walsh_cells else
-                           "force launch pair k_force_tc (tcgen05) + k_force_gen (concurrent streams)")
+                "kernel": ("force launch pair %s + %s (concurrent streams)" % (
+                    "k_force_wht32 (8-node cells, Walsh basis)" if walsh_cells else
+                    "k_force_tc (8-node cells, tcgen05)",
+                    "k_force_gen_tc (other patterns, tcgen05)" if hanging_tc else
+                    "k_force_gen (other patterns, FP32 SIMT)"))
                 if mixed else "k_force_simt<float>", "peak_source": "hbm_gbs " + pk_src}
         if mixed and not walsh_cells:
             roof["tensor_tflops_tf32"] = 3 * flops / t_force / 1e12
@@ -469,9 +482,11 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": {"fp64": "f64", "fp32": "f32 contraction, f64 state",
-                     "mixed": ("f32 contraction (8-node cells in the Walsh basis), f64 state"
+                     "mixed": ("f32 contraction (8-node cells in the Walsh basis)"
                                if walsh_cells else
-                               "tf32x3 contraction (f32 accumulate), f64 state")}[args.precision],
+                               "tf32x3 contraction (f32 accumulate)") +
+                              (", tf32x3 (f32 accumulate) for the other patterns"
+                               if hanging_tc else "") + ", f64 state"}[args.precision],
            "data": "synthetic",
            "config": {"workload": mesh.name + " (cube minus r=0.2 ball, levels 4-8, lognormal E)",
                       "cells": mesh.n_cells, "dof": mesh.n_dof, "patterns": len(S.masters),
@@ -515,8 +530,13 @@ def main():
         B = 64
         Bs = Solver.from_mesh(mb, precision="fp32", n_rhs=B, device=local, stream=stream.cuda_stream)
         Bs.initial()
+        # tile shapes per pattern class chosen by the autotuner on this GPU
+        from paper_2103_09100_gb300 import autotune
+        tuned = autotune.tune(Bs, steps=5, repeats=3, device_name=torch.cuda.get_device_name(local))
+        Bs.initial()
         Bs.step(3)
         kb = 200
+        L.sbx_prepare_steps(Bs.ctx, kb, Bs.dt, Bs.alpha)
         msb = time_steps(Bs, stream, kb, world, torch)
         nb_err = 100
         gb = gpu_after(Bs, nb_err, L).reshape(-1, B)
@@ -536,7 +556,10 @@ def main():
                             "step_hbm_frac": (bb_step / ((ms_fb + ms_ub) / 20 * 1e-3) / 1e9) / pk["hbm_gbs"],
                             "fp32_gflops": contraction_flops(nperb, B) / (ms_fb / 20 * 1e-3) / 1e9,
                             "rel_err_vs_oracle_max": max(errs), "err_cases": [0, 37],
-                            "err_steps": nb_err}
+                            "err_steps": nb_err,
+                            "autotune": {"params": {str(k): v for k, v in tuned["params"].items()},
+                                         "force_ms_default": tuned["force_ms_default"],
+                                         "force_ms_tuned": tuned["force_ms_tuned"]}}
         Bs.close()
         # config 4: the layered-trench octree (~9.5M cells), mixed, 500 steps
         mt = og.config_layered_trench()
@@ -546,13 +569,23 @@ def main():
         T.initial()
         T.step(3)
         kt = 500
+        L.sbx_prepare_steps(T.ctx, kt, T.dt, T.alpha)
         mst = time_steps(T, stream, kt, world, torch)
+        ut = gpu_after(T, kt, L)
+        n_pat = len(T.masters)
+        T.close()
+        # error of the 500 mixed steps against 500 FP64 steps of the same
+        # mesh on the GPU (the FP64 form is pinned to the oracle)
+        F = Solver.from_mesh(mt, precision="fp64", device=local, stream=stream.cuda_stream, dt=T.dt)
+        uf = gpu_after(F, kt, L)
+        F.close()
         forms["trench_mixed"] = {"value": world * mt.n_dof * kt / (mst * 1e-3), "unit": UNIT,
                                  "ms_per_step": mst / kt, "steps": kt,
                                  "workload": mt.name + " (%d cells, %d DOF, %d patterns)"
-                                 % (mt.n_cells, mt.n_dof, len(T.masters)),
-                                 "device_memory_gb": (free0 - free1) / 1e9}
-        T.close()
+                                 % (mt.n_cells, mt.n_dof, n_pat),
+                                 "cells": mt.n_cells, "dof": mt.n_dof, "patterns": n_pat,
+                                 "device_memory_gb": (free0 - free1) / 1e9,
+                                 "rel_err_vs_fp64_gpu_500_steps": rel_err(ut, uf)}
         # next-row workload: eigenfrequencies of the roller-supported 64^3
         # cube by the GPU Lanczos iteration (K applied by the FP64 force
         # kernel, full reorthogonalisation)

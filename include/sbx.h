@@ -130,9 +130,12 @@ int set_patterns(sbx_ctx *ctx, int n_patterns, const int32_t *n_nodes,
  *   n_rhs             number of load cases B advanced together (1 = plain).
  *   precision_mode    SBX_PREC_*.
  *   Cells are processed grouped by pattern; within a pattern the given order
- *   is kept (pass Morton order for locality).
- *   Errors: SBX_ESTATE (no patterns), SBX_EINVAL (ids out of range, node count
- *   mismatch, non-positive h/E/rho), SBX_ENOMEM.
+ *   is kept (pass Morton order for locality).  A node that no cell touches
+ *   gets zero mass and stays at rest (M^-1 = 0) until sbx_set_mass gives it
+ *   a mass (one part of a split mesh, see sbx_share_state).
+ *   Errors: SBX_ESTATE (no patterns; the state is shared with another
+ *   context), SBX_EINVAL (ids out of range, node count mismatch,
+ *   non-positive h/E/rho), SBX_ENOMEM.
  */
 int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells,
                 const int32_t *cell_pattern, const uint8_t *cell_sym,
@@ -400,20 +403,104 @@ int sbx_set_mass(sbx_ctx *ctx, const double *mass);
 int sbx_query(sbx_ctx *ctx, int what, int64_t *out);
 
 /*
+ * Node-cut interface sum with the neighbouring parts (Sec. 4.2: each part
+ * sums the partial internal forces of the DOFs it shares with its
+ * neighbours).  The caller moves the buffers between parts (e.g. NCCL
+ * send / receive); the library packs and sums on the context's stream.
+ * Rows follow the force accumulator (sbx_field_ptr(SBX_F_INT)): 3 doubles
+ * per node in the FP64 forms, 4 floats (x, y, z, unused) in the mixed form.
+ *
+ * sbx_halo_plan: n_send nodes (local ids; the blocks of all neighbours in
+ *   the caller's order) whose rows the pack writes, and for each of n_cut
+ *   cut nodes (local ids) its contributions contrib_src[contrib_ptr[j] ..
+ *   contrib_ptr[j+1]): -1 = this part's own partial force, r >= 0 = row r
+ *   of the receive buffer.  The sum adds them in that order from zero, so
+ *   parts that list a node's contributions in one common order (e.g. by
+ *   ascending rank of the holding part) compute identical sums.  Host or
+ *   device arrays (copied).  One load case only.
+ *   Errors: SBX_ESTATE (no mesh), SBX_EINVAL (ids or rows out of range,
+ *   contrib_ptr not starting at 0 or decreasing), SBX_ENOMEM.
+ * sbx_halo_pack: send_buf[i] = row send_nodes[i] of the force accumulator
+ *   (device memory, n_send rows).  Enqueued on the stream.
+ * sbx_halo_sum: for every cut node, the accumulator row = the sum of its
+ *   contributions (recv_buf: device memory, n_send rows, filled by the
+ *   neighbours in the same block order).  Enqueued on the stream.
+ */
+int sbx_halo_plan(sbx_ctx *ctx, int64_t n_send, const int64_t *send_nodes, int64_t n_cut,
+                  const int64_t *cut_nodes, const int64_t *contrib_ptr,
+                  const int64_t *contrib_src);
+int sbx_halo_pack(sbx_ctx *ctx, void *send_buf);
+int sbx_halo_sum(sbx_ctx *ctx, const void *recv_buf);
+
+/*
+ * sbx_share_state: make ctx (a mesh over the same n_nodes, load cases and
+ * precision, created on the same device and stream) a guest of owner: ctx
+ * releases its own state and afterwards reads the owner's U_n and adds its
+ * cells' internal forces into the owner's accumulator with sbx_force.  This
+ * splits one part's cells in two, e.g. the cells on the interface and the
+ * interior ones, so that the interface exchange can run while the interior
+ * force is computed (the computation order of Sec. 4.2).  A guest's other
+ * stepping calls fail with SBX_ESTATE; loads belong on the owner; the owner
+ * clears the accumulator in its sbx_update and is destroyed after its
+ * guests (sbx_destroy of an owner with guests: SBX_ESTATE).
+ *   Errors: SBX_EINVAL (sizes, devices or streams differ), SBX_ESTATE.
+ */
+int sbx_share_state(sbx_ctx *ctx, sbx_ctx *owner);
+
+/*
+ * sbx_classify_cells: the set-up's integer work on the GPU (Sec. 3.2.1 -
+ * 3.2.2, Alg. 1's set-up): every cell's master pattern (the largest mask of
+ * its mask's orbit under the 48 signed permutations), its op (the smallest
+ * op carrying it there; op convention of mesh_upload) and its node list in
+ * master node order; then the cells sorted by pattern (stable: the given
+ * order, e.g. Morton, is kept within a pattern) and each pattern's
+ * slot-major connectivity.  These are exactly the arrays mesh_upload takes
+ * and builds.
+ *   slot_node[C][26]  DEVICE, node id per slot (-1: absent), mesh format of
+ *                     the octree generator (corners, mid-edges, face centres).
+ *   mask[C]           DEVICE, 12-bit mid-edge mask.
+ *   masters, n_masters   HOST out: the distinct master masks, ascending
+ *                     (pattern id = position), at most 144.
+ *   cell_pattern[C], cell_sym[C], cell_ptr[C+1], cell_nodes[<= 26 C]
+ *                     DEVICE out: as mesh_upload's inputs.
+ *   order[C]          DEVICE out: sorted position -> cell.
+ *   pat_start[P+1]    HOST out: first sorted position of each pattern.
+ *   conn[<= 26 C]     DEVICE out: pattern p's block [n_p][C_p] at offset
+ *                     sum_{q<p} n_q C_q.
+ * Synchronises the stream.  Allocates scratch with cudaMalloc.
+ *   Errors: SBX_EINVAL (sizes, host pointers where device memory is
+ *   required, a cell without a node its pattern needs), SBX_ENOMEM,
+ *   SBX_ECUDA.
+ */
+int sbx_classify_cells(sbx_ctx *ctx, int64_t n_cells, const int32_t *slot_node,
+                       const int32_t *mask, int32_t *masters, int32_t *n_masters,
+                       int32_t *cell_pattern, uint8_t *cell_sym, int64_t *cell_ptr,
+                       int32_t *cell_nodes, int64_t *order, int64_t *pat_start, int32_t *conn);
+
+/*
  * sbx_set_launch / sbx_get_launch: launch configuration of the force
  * kernels (no counterpart in the paper: how Eq. Rintep's contraction is
  * mapped onto the GPU).  The results do not depend on it beyond rounding;
  * the step graphs are rebuilt after a change.
  *   SBX_LAUNCH_HANGING_KERNEL      mixed form: the patterns other than the
- *       identity-op 8-node cell on FP32 SIMT (SBX_HANGING_SIMT, the
- *       default) or on the tensor cores, TF32 x 3 with FP32 accumulation
- *       in tensor memory (SBX_HANGING_TENSOR).
+ *       identity-op 8-node cell on the tensor cores, TF32 x 3 with FP32
+ *       accumulation in tensor memory (SBX_HANGING_TENSOR, the default),
+ *       or on FP32 SIMT (SBX_HANGING_SIMT).
  *   SBX_LAUNCH_WALSH_CTAS_PER_SM   mixed form: resident CTAs per SM of the
  *       Walsh-basis kernel, 1 .. 8, or 0 for the library's choice.
- *   Errors: SBX_EINVAL (unknown parameter or value).
+ *   SBX_LAUNCH_BATCH_TILE_CELLS + c   batched form, pattern class c (0: up
+ *       to 8 nodes, 1: up to 16, 2: more): most cells per tile, 1 .. 64
+ *       (default 32).  A change rebuilds the class's tiles.
+ *   SBX_LAUNCH_BATCH_SMEM_KB + c      batched form, class c: shared memory
+ *       per CTA in KB that a tile's staging may take, 16 .. 227 (default
+ *       100: two CTAs per SM); tiles shrink until they fit.
+ *   Errors: SBX_EINVAL (unknown parameter or value; a tile shape that does
+ *   not fit leaves the previous one in place).
  */
 #define SBX_LAUNCH_HANGING_KERNEL     0
 #define SBX_LAUNCH_WALSH_CTAS_PER_SM  1
+#define SBX_LAUNCH_BATCH_TILE_CELLS   16
+#define SBX_LAUNCH_BATCH_SMEM_KB      20
 #define SBX_HANGING_SIMT   0
 #define SBX_HANGING_TENSOR 1
 int sbx_set_launch(sbx_ctx *ctx, int what, int value);

@@ -387,25 +387,51 @@ def config_multi_point(seed=2, lmin=3, lmax=7, n_points=8, r0=0.118, n_rhs=64):
     return m
 
 
-def config_layered_trench(seed=3, lmin=5, lmax=10, band=0.02):
-    """[0,4] x [0,4] x [0,2] as 2 x 2 x 1 roots of edge 2, levels 5-10 refined
-    toward a free-surface trench (x in [1.9, 2.1], depth 0.2, removed),
-    three horizontal layers with E = 1 : 4 : 16 from top to bottom."""
+def _layer_z1(x, y):
+    """Lower curved layer interface of the layered trench box."""
+    return 2.0 / 3.0 + 0.15 * np.sin(np.pi * x / 2.0) * np.cos(np.pi * y / 2.0)
+
+
+def _layer_z2(x, y):
+    """Upper curved layer interface of the layered trench box."""
+    return 4.0 / 3.0 + 0.10 * np.cos(np.pi * x) * np.sin(np.pi * y / 2.0)
+
+
+def config_layered_trench(seed=3, lmin=5, lmax=10, band=0.02, half_len=1.0, layer_level=8,
+                          p=0.002):
+    """[0,4] x [0,4] x [0,2] as 2 x 2 x 1 roots of edge 2, levels 5-10:
+    refined toward a free-surface trench of finite length (x in [1.9, 2.1],
+    y in [1, 3], depth 0.2, removed; refinement by the 3-D distance to it),
+    toward two curved layer interfaces (to level 8) and by seeded random
+    flags with probability p per cell and level; three layers between the
+    curved interfaces with E = 1 : 4 : 16 from top to bottom."""
+    rng = np.random.default_rng(seed + 1000)
+
     def trench(c):
-        return (np.abs(c[:, 0] - 2.0) < 0.1) & (c[:, 2] > 1.8)
+        return ((np.abs(c[:, 0] - 2.0) < 0.1) & (np.abs(c[:, 1] - 2.0) < half_len) &
+                (c[:, 2] > 1.8))
 
     def refine(q, c, hq):
         dx = np.maximum(np.abs(c[:, 0] - 2.0) - 0.1, 0.0)
+        dy = np.maximum(np.abs(c[:, 1] - 2.0) - half_len, 0.0)
         dz = np.maximum(1.8 - c[:, 2], 0.0)
-        return np.hypot(dx, dz) < band + 1.2 * hq
+        near_t = np.sqrt(dx * dx + dy * dy + dz * dz) < band + 1.2 * hq
+        dl = np.minimum(np.abs(c[:, 2] - _layer_z1(c[:, 0], c[:, 1])),
+                        np.abs(c[:, 2] - _layer_z2(c[:, 0], c[:, 1])))
+        near_l = (dl < 0.9 * hq) & (q < layer_level)
+        flags = (rng.random(len(c)) < p) & (q < lmax - 1)
+        return near_t | near_l | flags
 
     m = make_mesh("layered_trench_l5-10", (2, 2, 1), lmin, lmax, refine, h_root=2.0, remove=trench)
-    zc = (m.anchor[:, 2] + 0.5 * 2 ** (m.lmax - m.level.astype(np.int64))) * m.h_finest
-    m.E = np.where(zc > 4.0 / 3.0, 1.0, np.where(zc > 2.0 / 3.0, 4.0, 16.0))
+    S = 2 ** (m.lmax - m.level.astype(np.int64))
+    c = (m.anchor + 0.5 * S[:, None]) * m.h_finest + np.asarray(m.origin)[None, :]
+    m.E = np.where(c[:, 2] > _layer_z2(c[:, 0], c[:, 1]), 1.0,
+                   np.where(c[:, 2] > _layer_z1(c[:, 0], c[:, 1]), 4.0, 16.0))
     m.fixed_nodes = np.where(np.abs(m.node_xyz[:, 2]) < 1e-12)[0]
     top = nearest_node(m, (1.0, 2.0, 2.0))
     m.sources = [point_source(top, (0, 0, -1), ricker_t1_for_mesh(m))]
-    m.meta = {"seed": seed, "layers_E": [1, 4, 16]}
+    m.meta = {"seed": seed, "layers_E": [1, 4, 16], "trench": "x in [1.9, 2.1], y in [1, 3], z > 1.8",
+              "p": p}
     return m
 
 

@@ -220,3 +220,46 @@ def run_sparse(K, M_diag, dt, alpha, fixed, n_steps, u_c, u_p, fext=None, n0=0):
         u_n = (dt2minv * r + 2 * u_c - (1 - 0.5 * alpha * dt) * u_p) / (1 + 0.5 * alpha * dt)
         u_p, u_c = u_c, u_n
     return u_c, u_p
+
+
+def line_load_forces(mesh, a, b, q, tol=1e-9):
+    """Consistent nodal forces (magnitudes) of a uniform line load q along
+    the segment [a, b]: every cell edge piece between two consecutive nodes
+    of the edge that lies on the segment contributes q * length / 2 to each
+    of its two nodes, each physical piece once.  Returns {node: force}."""
+    from . import cube
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    d = b - a
+    L = float(np.linalg.norm(d))
+    x = np.asarray(mesh.node_xyz, float)
+
+    def on(pt):
+        t = float((pt - a) @ d) / (L * L)
+        return (np.linalg.norm(pt - a - t * d) <= tol * L) and -tol <= t <= 1 + tol
+
+    ends = []   # the two corner slots of each edge: the mid-edge's position with
+    for e in range(12):   # its coordinate along the edge set to -1 and +1
+        p = cube.SLOT_POS[8 + e].copy()
+        ax = e // 4
+        p0, p1 = p.copy(), p.copy()
+        p0[ax], p1[ax] = -1, 1
+        ends.append((cube.pos_to_slot(p0), cube.pos_to_slot(p1)))
+    pieces = set()
+    for c in range(mesh.n_cells):
+        for e in range(12):
+            c0, c1 = ends[e]
+            mid = 8 + e
+            seq = [mesh.slot_node[c, c0]]
+            if mesh.slot_node[c, mid] >= 0:
+                seq.append(mesh.slot_node[c, mid])
+            seq.append(mesh.slot_node[c, c1])
+            for u, v in zip(seq[:-1], seq[1:]):
+                if on(x[u]) and on(x[v]):
+                    pieces.add((min(u, v), max(u, v)))
+    out = {}
+    for u, v in sorted(pieces):
+        half = 0.5 * q * float(np.linalg.norm(x[u] - x[v]))
+        out[u] = out.get(u, 0.0) + half
+        out[v] = out.get(v, 0.0) + half
+    return out

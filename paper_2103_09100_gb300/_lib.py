@@ -29,8 +29,10 @@ EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patte
            "set_modulus", "sbx_adjoint", "sbx_force", "sbx_update", "sbx_field_ptr", "sbx_touch",
            "sbx_set_mass", "sbx_wait_selftest", "sbx_set_receivers", "sbx_read_history",
            "sbx_lanczos", "sbx_set_mixed_kernel", "sbx_prepare_steps", "sbx_set_launch",
-           "sbx_get_launch"]
+           "sbx_get_launch", "sbx_halo_plan", "sbx_halo_pack", "sbx_halo_sum", "sbx_share_state",
+           "sbx_classify_cells"]
 SBX_LAUNCH_HANGING_KERNEL, SBX_LAUNCH_WALSH_CTAS_PER_SM = 0, 1
+SBX_LAUNCH_BATCH_TILE_CELLS, SBX_LAUNCH_BATCH_SMEM_KB = 16, 20
 SBX_HANGING_SIMT, SBX_HANGING_TENSOR = 0, 1
 SBX_LAYOUT_F64_DOF, SBX_LAYOUT_F32_NODE4, SBX_LAYOUT_F32_DOF = 0, 1, 2
 SBX_Q_KERNELS_PER_STEP, SBX_Q_FORCE_LAUNCHES, SBX_Q_TILES, SBX_Q_BRICK_TILES = 0, 1, 2, 3
@@ -88,6 +90,11 @@ def load(path: str = LIB_PATH):
         "sbx_lanczos": [vp, i64, vp, vp, vp],
         "sbx_set_mixed_kernel": [vp, i32],
         "sbx_set_launch": [vp, i32, i32],
+        "sbx_halo_plan": [vp, i64, vp, i64, vp, vp, vp],
+        "sbx_halo_pack": [vp, vp],
+        "sbx_halo_sum": [vp, vp],
+        "sbx_share_state": [vp, vp],
+        "sbx_classify_cells": [vp, i64, vp, vp, vp, C.POINTER(i32), vp, vp, vp, vp, vp, vp, vp],
         "sbx_get_launch": [vp, i32, C.POINTER(i32)],
     }
     for name, args in sig.items():
@@ -245,6 +252,57 @@ def sbx_lanczos(ctx, k, v0):
     _check(ctx, load().sbx_lanczos(ctx, int(k), _ptr(v, np.float64), _ptr(alpha, np.float64),
                                    _ptr(beta, np.float64)))
     return alpha, beta
+
+
+def sbx_halo_plan(ctx, send_nodes, cut_nodes, contrib_ptr, contrib_src):
+    snd = np.ascontiguousarray(send_nodes, np.int64)
+    cut = np.ascontiguousarray(cut_nodes, np.int64)
+    ptr = np.ascontiguousarray(contrib_ptr, np.int64)
+    src = np.ascontiguousarray(contrib_src, np.int64)
+    _check(ctx, load().sbx_halo_plan(ctx, int(snd.size), _ptr(snd, np.int64) if snd.size else None,
+                                     int(cut.size), _ptr(cut, np.int64) if cut.size else None,
+                                     _ptr(ptr, np.int64), _ptr(src, np.int64) if src.size else None))
+
+
+def sbx_halo_pack(ctx, send_buf):
+    _check(ctx, load().sbx_halo_pack(ctx, _ptr(send_buf)))
+
+
+def sbx_halo_sum(ctx, recv_buf):
+    _check(ctx, load().sbx_halo_sum(ctx, _ptr(recv_buf)))
+
+
+def sbx_classify_cells(ctx, slot_node, mask):
+    """GPU classification, sort and connectivity of a mesh given as CUDA
+    tensors slot_node (C, 26) int32 and mask (C,) int32.  Returns
+    (masters, cell_pattern, cell_sym, cell_ptr, cell_nodes, order,
+    pat_start, conn): masters and pat_start as numpy arrays, the rest as
+    CUDA tensors (cell_nodes and conn trimmed to their length)."""
+    import torch
+    C_ = int(mask.numel())
+    dev = mask.device
+    pat = torch.empty(C_, dtype=torch.int32, device=dev)
+    sym = torch.empty(C_, dtype=torch.uint8, device=dev)
+    ptr = torch.empty(C_ + 1, dtype=torch.int64, device=dev)
+    nodes = torch.empty(26 * C_, dtype=torch.int32, device=dev)
+    order = torch.empty(C_, dtype=torch.int64, device=dev)
+    conn = torch.empty(26 * C_, dtype=torch.int32, device=dev)
+    masters = np.zeros(144, np.int32)
+    pstart = np.zeros(145, np.int64)
+    nm = C.c_int()
+    _check(ctx, load().sbx_classify_cells(ctx, C_, _ptr(slot_node, np.int32), _ptr(mask, np.int32),
+                                          _ptr(masters, np.int32), C.byref(nm), _ptr(pat, np.int32),
+                                          _ptr(sym, np.uint8), _ptr(ptr, np.int64),
+                                          _ptr(nodes, np.int32), _ptr(order, np.int64),
+                                          _ptr(pstart, np.int64), _ptr(conn, np.int32)))
+    P = nm.value
+    n_tot = int(ptr[-1].item())
+    return (masters[:P].copy(), pat, sym, ptr, nodes[:n_tot], order, pstart[:P + 1].copy(),
+            conn[:n_tot])
+
+
+def sbx_share_state(ctx, owner):
+    _check(ctx, load().sbx_share_state(ctx, owner))
 
 
 def sbx_set_launch(ctx, what, value):

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsbx.so")
 SOURCES = ["sbx_api.cu", "kernels_simt.cu", "kernels_static.cu", "kernels_tc.cu",
-           "kernels_batch.cu", "kernels_adjoint.cu", "kernels_eigen.cu"]
+           "kernels_batch.cu", "kernels_adjoint.cu", "kernels_eigen.cu", "kernels_halo.cu", "kernels_setup.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(HERE, "..", "include")]

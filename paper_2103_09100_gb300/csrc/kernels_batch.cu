@@ -32,7 +32,6 @@ namespace {
 constexpr int BT_THREADS = 256;   // 8 warps
 constexpr int BT_WARPS = 8;
 constexpr int BC = 32;            // load cases per chunk
-constexpr uint32_t BT_SMEM_TARGET = 100u * 1024u;   // two CTAs per SM
 
 __host__ __device__ inline uint32_t b16(uint32_t x) { return (x + 15u) & ~15u; }
 
@@ -332,9 +331,11 @@ int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vecto
   for (int p = 0; p < P; ++p) {
     const int np = ctx->pat_nodes[p], m = 3 * np, cls = class_of(m);
     int64_t c0 = 0;
+    const uint32_t target = (uint32_t)ctx->b_smem_kb[cls] * 1024u;
     while (c0 < cnt[p]) {
-      // largest tile (32 cells or fewer) whose staging fits the target
-      int nc = (int)std::min<int64_t>(32, cnt[p] - c0);
+      // largest tile (b_tile_cells[cls] cells or fewer) whose staging fits
+      // the class's shared-memory budget
+      int nc = (int)std::min<int64_t>(ctx->b_tile_cells[cls], cnt[p] - c0);
       std::vector<int32_t> nodes;
       std::vector<uint16_t> lid;
       for (;;) {
@@ -351,7 +352,7 @@ int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vecto
         }
         const uint32_t need = bsmem(CLASS_MM[cls], (int)nodes.size(),
                                     (int)brec_layout(nc, (int)nodes.size(), np).bytes, tsz).total;
-        if (need <= BT_SMEM_TARGET || nc == 1) break;
+        if (need <= target || nc == 1) break;
         nc = std::max(1, nc / 2);
       }
       const int nn = (int)nodes.size();
@@ -416,6 +417,12 @@ int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vecto
       return SBX_EINVAL;
     }
   }
+  if (ctx->prec == SBX_PREC_FP32) {   // the classes beyond the 8-node cell, tensor-core form
+    std::vector<char> use(P, 0);
+    for (int p = 0; p < P; ++p) use[p] = class_of(3 * ctx->pat_nodes[p]) > 0;
+    if (int rc = gt_setup(ctx, conn, conn_off, cnt, start, sym_sorted, scale_sorted, use, err))
+      return rc;
+  }
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     err = "stream synchronisation failed";
     return SBX_ECUDA;
@@ -456,8 +463,10 @@ static void launch_class(const sbx_ctx *ctx, int c, const T *K, const void *u, v
 cudaError_t launch_force_batch(const sbx_ctx *ctx, const void *u, void *f, double dt,
                                cudaStream_t s) {
   bool load_done = false;
+  // FP32 form: the hanging-node classes on the tensor cores (default)
+  const bool tc = ctx->prec == SBX_PREC_FP32 && ctx->hanging_tc && ctx->n_gt_tiles > 0;
   for (int c = 0; c < 3; ++c) {
-    if (ctx->n_b_tiles[c] == 0) continue;
+    if (ctx->n_b_tiles[c] == 0 || (tc && c > 0)) continue;
     LoadTable L = ctx->loads();
     if (load_done) L.n = 0;
     load_done = true;
@@ -465,6 +474,13 @@ cudaError_t launch_force_batch(const sbx_ctx *ctx, const void *u, void *f, doubl
       launch_class<double>(ctx, c, ctx->d_K64, u, f, L, dt, s);
     else
       launch_class<float>(ctx, c, ctx->d_K32, u, f, L, dt, s);
+  }
+  if (tc) {
+    LoadTable L = ctx->loads();
+    if (load_done) L.n = 0;
+    cudaError_t e = launch_force_batch_tc(ctx, reinterpret_cast<const float *>(u),
+                                          reinterpret_cast<float *>(f), dt, L, s);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

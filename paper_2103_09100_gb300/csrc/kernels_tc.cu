@@ -1069,6 +1069,228 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   if (warp == 0) tc::tmem_dealloc(taddr, GT_COLS);
 }
 
+// ------------------------- hanging-node patterns of the batched form, tcgen05
+// k_force_batch_tc: the batched FP32 form's cells of every pattern other
+// than the 8-node cell, on the tensor cores.  Fields [node][3][B] (entry
+// (3 node + d) B + b); U_n as (hi, lo) FP32 pairs (float2).  Work item =
+// (record of up to 128 cells of one pattern -- the k_force_gen_tc records
+// and B blocks --, chunk of 32 load cases, a quarter of the record's
+// cells); persistent CTAs over contiguous ranges of items.
+// Per item, groups of 4 cells: TMEM lane 32 w + l = (cell 4 g + w, case
+// 32 chunk + l) with warp w and lane l, so A (128 x KP) holds the 128
+// (cell, case) rows of master-frame differences to slot 0, and D = A B^T
+// (TF32 x 3 as above) their forces; the epilogue adds each row's node
+// forces to f, coalesced over the warp's 32 cases.
+constexpr int BTC_THREADS = 128;
+
+__global__ void __launch_bounds__(BTC_THREADS, 2)
+    k_force_batch_tc(const TcTile *__restrict__ tiles, int ntiles, int nchunks,
+                     const uint8_t *__restrict__ recs, const float *__restrict__ Bg,
+                     const int64_t *__restrict__ boff, const float2 *__restrict__ u,
+                     float *__restrict__ f, int B, LoadTable Ld, const int64_t *__restrict__ d_step,
+                     double dt, int32_t *flags) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [0] record, [1] B, [2] MMA
+  uint32_t *taddr_s = reinterpret_cast<uint32_t *>(smem + 32);
+  float *Bs = reinterpret_cast<float *>(smem + GT_B_OFF);
+  unsigned char *rec = smem + GT_REC_OFF;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x;
+  const uint32_t mb_rec = tc::smem_addr(&mbar[0]), mb_b = mb_rec + 8u, mb_mma = mb_rec + 16u;
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_addr(taddr_s), GT_COLS);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(mb_rec, 1);
+    tc::mbar_init(mb_b, 1);
+    tc::mbar_init(mb_mma, 1);
+    tc::mbar_fence_init();
+  }
+  if (blockIdx.x == 0 && Ld.n > 0) {
+    const double t = (double)(*d_step) * dt;
+    for (int l = tid; l < Ld.n; l += BTC_THREADS)
+      atomicAdd(&f[Ld.dof[l]], (float)(-Ld.amp[l] * wavelet_value(Ld.kind[l], t, Ld.t1[l], Ld.ncyc[l])));
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = *taddr_s;
+  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  uint32_t ph_rec = 0u, ph_b = 0u, ph_mma = 0u;
+  bool pend_rec = false, pend_b = false, pend_mma = false, ok = true;
+  int cur_tile = -1, bpat = -1;
+  // items = (tile, chunk, quarter: 8 groups of 4 cells); CTA b takes a
+  // contiguous range of them, so that it reuses the record and B
+  const int per_tile = nchunks * 4, items = ntiles * per_tile;
+  const int it0 = (int)((int64_t)items * blockIdx.x / G);
+  const int it1 = (int)((int64_t)items * (blockIdx.x + 1) / G);
+  for (int item = it0; ok && item < it1; ++item) {
+    const int tile = item / per_tile, rem = item - tile * per_tile;
+    const int chunk = rem >> 2, quarter = rem & 3;
+    if (tile != cur_tile) {   // this item's record (and B when the pattern changes)
+      const TcTile T = tiles[tile];
+      if (tid == 0) {
+        tc::fence_proxy_async_smem();
+        tc::mbar_arrive_expect_tx(mb_rec, (uint32_t)T.rec_bytes);
+        tc::bulk_g2s(tc::smem_addr(rec), recs + T.rec_off, (uint32_t)T.rec_bytes, mb_rec);
+      }
+      pend_rec = true;
+      if (T.pat != bpat) {
+        if (tid == 0) {
+          const int64_t o = boff[T.pat];
+          const uint32_t bytes = (uint32_t)(boff[T.pat + 1] - o) * 4u;
+          tc::fence_proxy_async_smem();
+          tc::mbar_arrive_expect_tx(mb_b, bytes);
+          tc::bulk_g2s(tc::smem_addr(Bs), Bg + o, bytes, mb_b);
+        }
+        pend_b = true;
+        bpat = T.pat;
+      }
+      bool got = tc::mbar_wait_bounded(mb_rec, ph_rec, WAIT_POLLS);
+      if (pend_b) got = tc::mbar_wait_bounded(mb_b, ph_b, WAIT_POLLS) && got;
+      ok = __syncthreads_and(got);
+      if (!ok) break;
+      ph_rec ^= 1u;
+      pend_rec = false;
+      if (pend_b) {
+        ph_b ^= 1u;
+        pend_b = false;
+      }
+      cur_tile = tile;
+    }
+    const int32_t *hdr = reinterpret_cast<const int32_t *>(rec);
+    const int ncell = hdr[1], n = hdr[2], m = 3 * n;
+    const int KP = gt_kp(m), NP = gt_np(m);
+    const GtRec R = gt_rec_layout(n);
+    const float *scl = reinterpret_cast<const float *>(rec + R.scale);
+    const int32_t *ids = reinterpret_cast<const int32_t *>(rec + R.ids);
+    const int64_t b = (int64_t)chunk * 32 + lane;
+    for (int g = 8 * quarter; ok && g < 8 * quarter + 8 && 4 * g < ncell; ++g) {
+      const int c = 4 * g + warp;
+      const bool live = c < ncell;
+      const int op = live ? (int)rec[R.sym + c] : 0;
+      int sg[3], pm[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        sg[r] = (op >> r) & 1;
+        pm[r] = op_perm_of(op, r);
+      }
+      // A: this (cell, case) row's master-frame differences to slot 0
+      {
+        float2 ref[3];
+        const int64_t n0 = live ? ids[c] : 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          ref[a] = live ? u[(3 * n0 + a) * B + b] : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int q = 0; q < GT_GROUPS; ++q) {
+          if (24 * q >= KP) break;   // uniform
+          float x[24];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int k = 8 * q + j;
+            float d[3] = {0.0f, 0.0f, 0.0f};
+            if (live && k < n) {
+              const int64_t nk = ids[k * 128 + c];
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                const float2 v = u[(3 * nk + a) * B + b];
+                d[a] = (v.x - ref[a].x) + (v.y - ref[a].y);
+              }
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              const float y = pm[r] == 0 ? d[0] : (pm[r] == 1 ? d[1] : d[2]);
+              x[3 * j + r] = sg[r] ? -y : y;
+            }
+          }
+#pragma unroll
+          for (int h = 0; h < 3; ++h) {
+            const int ks = 3 * q + h;
+            if (8 * ks >= KP) break;
+            float h8[8], l8[8];
+#pragma unroll
+            for (int z = 0; z < 8; ++z) {
+              h8[z] = tc::to_tf32(x[8 * h + z]);
+              l8[z] = tc::to_tf32(x[8 * h + z] - h8[z]);
+            }
+            tc::tmem_st8(taddr + lane_base + GT_COL_A + 16u * (uint32_t)ks, h8);
+            tc::tmem_st8(taddr + lane_base + GT_COL_A + 16u * (uint32_t)ks + 8u, l8);
+          }
+        }
+        tc::tmem_st_wait();
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (tid == 0) {
+        const uint32_t idesc = tc::idesc_tf32(128, NP);
+        const uint32_t b_hi = tc::smem_addr(Bs), b_lo = b_hi + (uint32_t)(NP * KP) * 4u;
+        const uint32_t sbo = (uint32_t)(KP / 4) * 128u;
+        for (int ks = 0; ks < KP / 8; ++ks) {
+          const uint32_t o = (uint32_t)ks * 256u;
+          const uint64_t bh = tc::smem_desc(b_hi + o, 128, sbo), bl = tc::smem_desc(b_lo + o, 128, sbo);
+          const uint32_t ah = taddr + GT_COL_A + 16u * (uint32_t)ks, al = ah + 8u;
+          tc::mma_tf32_ta(taddr, ah, bh, idesc, ks > 0 ? 1u : 0u);
+          tc::mma_tf32_ta(taddr, ah, bl, idesc, 1u);
+          tc::mma_tf32_ta(taddr, al, bh, idesc, 1u);
+        }
+        tc::mma_commit(mb_mma);
+      }
+      pend_mma = true;
+      ok = __syncthreads_and(tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_POLLS));
+      tc::fence_after_sync();
+      if (!ok) break;
+      ph_mma ^= 1u;
+      pend_mma = false;
+      // epilogue: the row's forces times E h, back to the cell frame
+      const float sc = live ? scl[c] : 0.0f;
+#pragma unroll
+      for (int q = 0; q < GT_GROUPS; ++q) {
+        if (24 * q >= NP) break;   // uniform
+        float v[24];
+#pragma unroll
+        for (int h = 0; h < 3; ++h) {
+          float v8[8];
+          if (24 * q + 8 * h < NP) {
+            tc::tmem_ld8(taddr + lane_base + (uint32_t)(24 * q + 8 * h), v8);
+          } else {
+#pragma unroll
+            for (int z = 0; z < 8; ++z) v8[z] = 0.0f;
+          }
+#pragma unroll
+          for (int z = 0; z < 8; ++z) v[8 * h + z] = v8[z];
+        }
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int k = 8 * q + j;
+          if (!live || k >= n) continue;
+          const int64_t nk = ids[k * 128 + c];
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const float fv = sc * v[3 * j + r];
+            atomicAdd(&f[(3 * nk + pm[r]) * B + b], sg[r] ? -fv : fv);
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+    }
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(flags, 2);
+    if (pend_rec) tc::mbar_wait_bounded(mb_rec, ph_rec, WAIT_POLLS);
+    if (pend_b) tc::mbar_wait_bounded(mb_b, ph_b, WAIT_POLLS);
+    if (pend_mma) tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_POLLS);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, GT_COLS);
+}
+
 // Self-test of the bounded completion wait every tensor-core kernel uses:
 // one thread waits on a fresh mbarrier (arrived on first when `arrive`),
 // giving up after `polls` polls; a give-up sets bit 2 of the flags, which
@@ -1105,6 +1327,100 @@ void put(std::vector<uint8_t> &buf, size_t at, const T *src, size_t n) {
 
 }  // namespace
 
+// Tables of the tensor-core kernels for the patterns marked in `use`: per
+// pattern B = K_p as TF32 hi | lo in the canonical layout (offsets in
+// floats, boff[P] = end; patterns not used get an empty range) and records
+// of up to 128 consecutive cells, heaviest first.
+int gt_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<int64_t> &conn_off,
+             const std::vector<int64_t> &cnt, const std::vector<int64_t> &start,
+             const std::vector<uint8_t> &sym_sorted, const std::vector<double> &scale_sorted,
+             const std::vector<char> &use, std::string &err) {
+  const int P = ctx->n_pat;
+  std::vector<float> Bgt;
+  std::vector<int64_t> boff(P + 1, 0);
+  std::vector<uint8_t> recs;
+  std::vector<std::pair<int64_t, TcTile>> tl;   // (cost, tile)
+  int nmax = 1;
+  for (int p = 0; p < P; ++p) {
+    boff[p] = (int64_t)Bgt.size();
+    if (!use[p] || cnt[p] == 0) continue;
+    const int np = ctx->pat_nodes[p], m = 3 * np;
+    const int KP = gt_kp(m), NP = gt_np(m), NKc = KP / 4;
+    Bgt.resize(Bgt.size() + 2 * (size_t)NP * KP, 0.0f);
+    float *Bh = Bgt.data() + boff[p], *Bl = Bh + (size_t)NP * KP;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        const double kv = ctx->K_host[ctx->pat_koff[p] + (int64_t)i * m + j];
+        const float hi = tf32_round_host((float)kv);
+        const float lo = tf32_round_host((float)(kv - (double)hi));
+        const size_t o = (size_t)(i >> 3) * NKc * 32 + (j >> 2) * 32 + (i & 7) * 4 + (j & 3);
+        Bh[o] = hi;
+        Bl[o] = lo;
+      }
+    nmax = std::max(nmax, np);
+    const GtRec R = gt_rec_layout(np);
+    const int64_t Cp = cnt[p];
+    for (int64_t c0 = 0; c0 < Cp; c0 += 128) {
+      const int nc = (int)std::min<int64_t>(128, Cp - c0);
+      const size_t at = recs.size();
+      recs.resize(at + R.bytes, 0);
+      const int32_t hdr[4] = {p, nc, np, 0};
+      put(recs, at, hdr, 4);
+      std::vector<float> sc(128, 0.0f);
+      std::vector<uint8_t> sy(128, 0);
+      std::vector<int32_t> ids((size_t)np * 128, 0);
+      for (int c = 0; c < nc; ++c) {
+        sc[c] = (float)scale_sorted[start[p] + c0 + c];
+        sy[c] = sym_sorted[start[p] + c0 + c];
+        for (int k = 0; k < np; ++k)
+          ids[(size_t)k * 128 + c] = conn[conn_off[p] + (int64_t)k * Cp + c0 + c];
+      }
+      put(recs, at + R.scale, sc.data(), 128);
+      put(recs, at + R.sym, sy.data(), 128);
+      put(recs, at + R.ids, ids.data(), ids.size());
+      TcTile t;
+      t.rec_off = (int64_t)at;
+      t.rec_bytes = (int32_t)R.bytes;
+      t.pat = p;
+      tl.emplace_back((int64_t)NP * KP * nc, t);
+    }
+  }
+  boff[P] = (int64_t)Bgt.size();
+  std::stable_sort(tl.begin(), tl.end(),
+                   [](const std::pair<int64_t, TcTile> &a, const std::pair<int64_t, TcTile> &b) {
+                     return a.first > b.first;
+                   });
+  std::vector<TcTile> tiles;
+  for (auto &x : tl) tiles.push_back(x.second);
+  auto up = [&](auto **dst, const auto &vec) -> int {
+    using T = typename std::remove_reference<decltype(vec)>::type::value_type;
+    if (*dst) cudaFree(*dst);
+    *dst = nullptr;
+    if (cudaMalloc((void **)dst, std::max<size_t>(vec.size(), 1) * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      err = "cudaMalloc failed (tensor-core pattern tables)";
+      return SBX_ENOMEM;
+    }
+    if (!vec.empty() && cudaMemcpyAsync(*dst, vec.data(), vec.size() * sizeof(T),
+                                        cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+      err = "copy of tensor-core pattern tables failed";
+      return SBX_ECUDA;
+    }
+    return SBX_OK;
+  };
+  if (int rc = up(&ctx->d_gt_B, Bgt)) return rc;
+  if (int rc = up(&ctx->d_gt_boff, boff)) return rc;
+  if (int rc = up(&ctx->d_gt_rec, recs)) return rc;
+  if (int rc = up(&ctx->d_gt_tiles, tiles)) return rc;
+  ctx->n_gt_tiles = (int)tiles.size();
+  ctx->gt_smem = gt_smem_bytes(nmax);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    err = "stream synchronisation failed";
+    return SBX_ECUDA;
+  }
+  return SBX_OK;
+}
+
 // Host preparation: tile records of the 8-node cell (tensor-core kernel) and
 // 32-cell tiles of every other pattern.
 int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<int64_t> &conn_off,
@@ -1122,14 +1438,7 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   std::vector<int64_t> mark(ctx->N, -1);   // node -> last tile that holds it
   int64_t stamp = 0;
   ctx->n_brick_tiles = 0;
-  // k_force_gen_tc: per pattern B (TF32 hi | lo, canonical layout; offsets in
-  // floats, boff[P] = end) and 128-cell tile records
-  std::vector<float> Bgt;
-  std::vector<int64_t> boff(P + 1, 0);
-  std::vector<uint8_t> gt_recs;
-  std::vector<std::pair<int64_t, TcTile>> gt_tiles;   // (cost, tile)
-  std::vector<char> gt_has(P, 0);
-  int gt_nmax = 1;
+
   for (int p = 0; p < P; ++p) {
     if (cnt[p] == 0) continue;
     const int np = ctx->pat_nodes[p], m = 3 * np;
@@ -1150,50 +1459,6 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
         gen.push_back(t);
       }
       gen_mmax = std::max(gen_mmax, m);
-      // tensor-core form: B_p, then records of up to 128 cells
-      {
-        const int KP = gt_kp(m), NP = gt_np(m), NKc = KP / 4;
-        boff[p] = (int64_t)Bgt.size();
-        gt_has[p] = 1;
-        Bgt.resize(Bgt.size() + 2 * (size_t)NP * KP, 0.0f);
-        float *Bh = Bgt.data() + boff[p], *Bl = Bh + (size_t)NP * KP;
-        for (int i = 0; i < m; ++i)
-          for (int j = 0; j < m; ++j) {
-            const double kv = ctx->K_host[ctx->pat_koff[p] + (int64_t)i * m + j];
-            const float hi = tf32_round_host((float)kv);
-            const float lo = tf32_round_host((float)(kv - (double)hi));
-            const size_t o = (size_t)(i >> 3) * NKc * 32 + (j >> 2) * 32 + (i & 7) * 4 + (j & 3);
-            Bh[o] = hi;
-            Bl[o] = lo;
-          }
-        gt_nmax = std::max(gt_nmax, np);
-        const GtRec R = gt_rec_layout(np);
-        const int64_t Cp = cnt[p];
-        for (int64_t c0 = 0; c0 < Cp; c0 += 128) {
-          const int nc = (int)std::min<int64_t>(128, Cp - c0);
-          const size_t at = gt_recs.size();
-          gt_recs.resize(at + R.bytes, 0);
-          const int32_t hdr[4] = {p, nc, np, 0};
-          put(gt_recs, at, hdr, 4);
-          std::vector<float> sc(128, 0.0f);
-          std::vector<uint8_t> sy(128, 0);
-          std::vector<int32_t> ids((size_t)np * 128, 0);
-          for (int c = 0; c < nc; ++c) {
-            sc[c] = (float)scale_sorted[start[p] + c0 + c];
-            sy[c] = sym_sorted[start[p] + c0 + c];
-            for (int k = 0; k < np; ++k)
-              ids[(size_t)k * 128 + c] = conn[conn_off[p] + (int64_t)k * Cp + c0 + c];
-          }
-          put(gt_recs, at + R.scale, sc.data(), 128);
-          put(gt_recs, at + R.sym, sy.data(), 128);
-          put(gt_recs, at + R.ids, ids.data(), ids.size());
-          TcTile t;
-          t.rec_off = (int64_t)at;
-          t.rec_bytes = (int32_t)R.bytes;
-          t.pat = p;
-          gt_tiles.emplace_back((int64_t)NP * KP * nc, t);
-        }
-      }
       continue;
     }
     // B = K_p hi | lo in the canonical layout (rows 24 .. 31 zero)
@@ -1368,23 +1633,11 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   if (int rc = up(&ctx->d_gen_tiles, gen)) return rc;
   if (int rc = up(&ctx->d_gen_K, Kpad)) return rc;
   if (int rc = up(&ctx->d_gen_koff, kpoff)) return rc;
-  {   // tensor-core form of the other patterns: heaviest tiles first;
-      // patterns without a B block get an empty range
-    boff[P] = (int64_t)Bgt.size();
-    for (int p = P - 1; p >= 0; --p)
-      if (!gt_has[p]) boff[p] = boff[p + 1];
-    std::stable_sort(gt_tiles.begin(), gt_tiles.end(),
-                     [](const std::pair<int64_t, TcTile> &a, const std::pair<int64_t, TcTile> &b) {
-                       return a.first > b.first;
-                     });
-    std::vector<TcTile> gtt;
-    for (auto &x : gt_tiles) gtt.push_back(x.second);
-    if (int rc = up(&ctx->d_gt_B, Bgt)) return rc;
-    if (int rc = up(&ctx->d_gt_boff, boff)) return rc;
-    if (int rc = up(&ctx->d_gt_rec, gt_recs)) return rc;
-    if (int rc = up(&ctx->d_gt_tiles, gtt)) return rc;
-    ctx->n_gt_tiles = (int)gtt.size();
-    ctx->gt_smem = gt_smem_bytes(gt_nmax);
+  {   // the other patterns in the tensor-core form as well
+    std::vector<char> use(P, 0);
+    for (const Tile &t : gen) use[t.pat] = 1;
+    if (int rc = gt_setup(ctx, conn, conn_off, cnt, start, sym_sorted, scale_sorted, use, err))
+      return rc;
   }
   const int64_t nt = (int64_t)tiles.size();
   ctx->n_tc_tiles[0] = (int)nt;
@@ -1435,8 +1688,22 @@ cudaError_t prepare_tc_kernels() {
   e = cudaFuncSetAttribute(k_force_gen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)gt_smem_bytes(26));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_force_batch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)gt_smem_bytes(26));
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_force_gen, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)gen_smem(78));
+}
+
+cudaError_t launch_force_batch_tc(const sbx_ctx *ctx, const float *pairs, float *f, double dt,
+                                  LoadTable L, cudaStream_t s) {
+  const int nchunks = ctx->B / 32;
+  const int items = ctx->n_gt_tiles * nchunks * 4;
+  const int grid = std::max(1, std::min(items, 2 * ctx->n_sm));
+  k_force_batch_tc<<<grid, BTC_THREADS, ctx->gt_smem, s>>>(
+      ctx->d_gt_tiles, ctx->n_gt_tiles, nchunks, ctx->d_gt_rec, ctx->d_gt_B, ctx->d_gt_boff,
+      reinterpret_cast<const float2 *>(pairs), f, ctx->B, L, ctx->d_step, dt, ctx->d_flags);
+  return cudaGetLastError();
 }
 
 // The kernel of the regular cells and the kernel of the other patterns run

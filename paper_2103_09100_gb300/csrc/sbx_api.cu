@@ -110,6 +110,15 @@ void drop_graph(sbx_ctx *ctx) {
 
 void free_mesh(sbx_ctx *ctx) {
   drop_graph(ctx);
+  if (sbx_ctx *o = ctx->state_owner) {   // the state buffers are the owner's
+    ctx->d_u[0] = ctx->d_u[1] = nullptr;
+    ctx->d_f = nullptr;
+    ctx->d_pair = nullptr;
+    o->n_guests -= 1;
+    ctx->state_owner = nullptr;
+  }
+  dfree(ctx->d_halo_send); dfree(ctx->d_halo_cut); dfree(ctx->d_halo_ptr); dfree(ctx->d_halo_src);
+  ctx->halo_n_send = ctx->halo_n_cut = 0;
   dfree(ctx->d_conn); dfree(ctx->d_conn_off); dfree(ctx->d_pat_cstart); dfree(ctx->d_pat_ccount);
   dfree(ctx->d_sym); dfree(ctx->d_scale); dfree(ctx->d_minv); dfree(ctx->d_mass);
   dfree(ctx->d_w);
@@ -338,6 +347,8 @@ int sbx_create(sbx_ctx **out, int device, void *cuda_stream) {
 
 int sbx_destroy(sbx_ctx *ctx) {
   if (!ctx) return SBX_OK;
+  if (ctx->n_guests > 0)
+    return fail(ctx, SBX_ESTATE, "other contexts share this context's state: destroy them first");
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   free_mesh(ctx);
@@ -428,6 +439,8 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   if (int rc = set_device(ctx)) return rc;
   ctx->err.clear();
   if (ctx->n_pat == 0) return fail(ctx, SBX_ESTATE, "set_patterns must come before mesh_upload");
+  if (ctx->n_guests > 0 || ctx->state_owner)
+    return fail(ctx, SBX_ESTATE, "the state is shared with another context");
   if (n_nodes < 1 || n_cells < 1 || n_nodes > (int64_t)INT32_MAX)
     return fail(ctx, SBX_EINVAL, "n_nodes / n_cells out of range");
   if (n_rhs != 1 && (n_rhs < 32 || n_rhs % 32 != 0 || n_rhs > 1024))
@@ -506,8 +519,9 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   }
   std::vector<double> minv(ndof);
   for (int64_t d = 0; d < ndof; ++d) {
-    if (!(mass[d] > 0)) return fail(ctx, SBX_EINVAL, "a node has no positive mass (unused node id?)");
-    minv[d] = 1.0 / mass[d];
+    if (mass[d] < 0 || !isfinite(mass[d])) return fail(ctx, SBX_EINVAL, "negative or non-finite mass");
+    // a node no cell touches has no mass and stays at rest until sbx_set_mass
+    minv[d] = mass[d] > 0 ? 1.0 / mass[d] : 0.0;
   }
   for (int64_t i = 0; i < n_fixed; ++i) minv[fixed[i]] = 0.0;
 
@@ -599,6 +613,12 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   for (int64_t s = 0; s < n_cells; ++s) ctx->h_hs[s] = hv[order[s]];
   if (n_rhs > 1) {
     std::string e;
+    ctx->hb_conn = conn;
+    ctx->hb_conn_off = conn_off;
+    ctx->hb_cnt = cnt;
+    ctx->hb_start = start;
+    ctx->hb_sym = ssym;
+    ctx->hb_scale = scale;
     const int brc = sbx::batch_setup(ctx, conn, conn_off, cnt, ssym, scale, start, e);
     if (brc) {
       free_mesh(ctx);
@@ -701,6 +721,7 @@ int set_load(sbx_ctx *ctx, int n_src, const int64_t *node, const double *dir3, c
 
 int set_initial(sbx_ctx *ctx, const double *u0, const double *v0, double dt, double alpha) {
   if (!ctx) return SBX_EINVAL;
+  if (ctx->state_owner) return fail(ctx, SBX_ESTATE, "this context shares another context's state: only sbx_force applies");
   if (int rc = set_device(ctx)) return rc;
   ctx->err.clear();
   if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before set_initial");
@@ -743,6 +764,7 @@ int set_initial(sbx_ctx *ctx, const double *u0, const double *v0, double dt, dou
 
 int step_n(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha) {
   if (!ctx) return SBX_EINVAL;
+  if (ctx->state_owner) return fail(ctx, SBX_ESTATE, "this context shares another context's state: only sbx_force applies");
   if (int rc = set_device(ctx)) return rc;
   ctx->err.clear();
   if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before step_n");
@@ -779,6 +801,7 @@ int step_n(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha) {
 
 int sbx_prepare_steps(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha) {
   if (!ctx) return SBX_EINVAL;
+  if (ctx->state_owner) return fail(ctx, SBX_ESTATE, "this context shares another context's state: only sbx_force applies");
   if (int rc = set_device(ctx)) return rc;
   ctx->err.clear();
   if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before sbx_prepare_steps");
@@ -792,6 +815,7 @@ int sbx_prepare_steps(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha) {
 int sbx_profile(sbx_ctx *ctx, int64_t n_steps, double dt, double alpha, double *ms_force,
                 double *ms_update) {
   if (!ctx || !ms_force || !ms_update) return SBX_EINVAL;
+  if (ctx->state_owner) return fail(ctx, SBX_ESTATE, "this context shares another context's state: only sbx_force applies");
   if (int rc = set_device(ctx)) return rc;
   ctx->err.clear();
   if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before sbx_profile");
@@ -862,6 +886,7 @@ int set_modulus(sbx_ctx *ctx, const double *E) {
 int sbx_adjoint(sbx_ctx *ctx, int64_t n_steps, double dt, int64_t n_rec, const int64_t *rec_dof,
                 const double *data, int64_t ckpt_every, double *misfit_out, double *grad_E_out) {
   if (!ctx) return SBX_EINVAL;
+  if (ctx->state_owner) return fail(ctx, SBX_ESTATE, "this context shares another context's state: only sbx_force applies");
   if (int rc = set_device(ctx)) return rc;
   ctx->err.clear();
   if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
@@ -984,6 +1009,19 @@ int sbx_force(sbx_ctx *ctx, double dt) {
   if (int rc = set_device(ctx)) return rc;
   ctx->err.clear();
   if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before sbx_force");
+  if (sbx_ctx *o = ctx->state_owner) {
+    // add this context's cells into the owner's accumulator, from the
+    // owner's current U_n (the owner clears the accumulator in its update)
+    if (!(dt > 0) || !isfinite(dt)) return fail(ctx, SBX_EINVAL, "dt must be > 0");
+    if (o->f_dirty) return fail(ctx, SBX_ESTATE, "the owner's force buffer holds a finished step");
+    ctx->cur = o->cur;
+    ctx->pair_of = o->pair_of;
+    ctx->step = o->step;
+    if (int rc = ensure_pairs(ctx)) return rc;
+    o->pair_of = ctx->pair_of;
+    if (int rc = force(ctx, ctx->d_u[ctx->cur], ctx->d_f, dt)) return rc;
+    return SBX_OK;
+  }
   if (ctx->f_pending) return fail(ctx, SBX_ESTATE, "sbx_force twice without sbx_update");
   if (!(dt > 0) || !isfinite(dt)) return fail(ctx, SBX_EINVAL, "dt must be > 0");
   if (ctx->f_dirty) {
@@ -998,6 +1036,7 @@ int sbx_force(sbx_ctx *ctx, double dt) {
 
 int sbx_update(sbx_ctx *ctx, double dt, double alpha) {
   if (!ctx) return SBX_EINVAL;
+  if (ctx->state_owner) return fail(ctx, SBX_ESTATE, "this context shares another context's state: only sbx_force applies");
   if (int rc = set_device(ctx)) return rc;
   ctx->err.clear();
   if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before sbx_update");
@@ -1062,6 +1101,7 @@ int sbx_touch(sbx_ctx *ctx) {
 
 int sbx_lanczos(sbx_ctx *ctx, int64_t k, const double *v0, double *alpha, double *beta) {
   if (!ctx) return SBX_EINVAL;
+  if (ctx->state_owner) return fail(ctx, SBX_ESTATE, "this context shares another context's state: only sbx_force applies");
   if (int rc = set_device(ctx)) return rc;
   ctx->err.clear();
   if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
@@ -1112,6 +1152,186 @@ int sbx_set_mixed_kernel(sbx_ctx *ctx, int kind) {
   return SBX_OK;
 }
 
+int sbx_halo_plan(sbx_ctx *ctx, int64_t n_send, const int64_t *send_nodes, int64_t n_cut,
+                  const int64_t *cut_nodes, const int64_t *contrib_ptr,
+                  const int64_t *contrib_src) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "mesh_upload must come before sbx_halo_plan");
+  if (ctx->B != 1) return fail(ctx, SBX_EINVAL, "the interface sum is for one load case");
+  if (n_send < 0 || n_cut < 0 || (n_send > 0 && !send_nodes) ||
+      (n_cut > 0 && (!cut_nodes || !contrib_ptr)))
+    return fail(ctx, SBX_EINVAL, "bad halo plan sizes or null arrays");
+  std::vector<int64_t> snd, cut, ptr, src;
+  if (int rc = fetch_vec(ctx, snd, send_nodes, (size_t)n_send)) return rc;
+  if (int rc = fetch_vec(ctx, cut, cut_nodes, (size_t)n_cut)) return rc;
+  if (n_cut > 0) {
+    if (int rc = fetch_vec(ctx, ptr, contrib_ptr, (size_t)n_cut + 1)) return rc;
+  } else {
+    ptr.assign(1, 0);
+  }
+  if (ptr[0] != 0) return fail(ctx, SBX_EINVAL, "contrib_ptr must start at 0");
+  for (int64_t j = 0; j < n_cut; ++j)
+    if (ptr[j + 1] < ptr[j]) return fail(ctx, SBX_EINVAL, "contrib_ptr must not decrease");
+  if (ptr[n_cut] > 0 && !contrib_src) return fail(ctx, SBX_EINVAL, "null contrib_src");
+  if (int rc = fetch_vec(ctx, src, contrib_src, (size_t)ptr[n_cut])) return rc;
+  for (int64_t v : snd)
+    if (v < 0 || v >= ctx->N) return fail(ctx, SBX_EINVAL, "send node out of range");
+  for (int64_t v : cut)
+    if (v < 0 || v >= ctx->N) return fail(ctx, SBX_EINVAL, "cut node out of range");
+  for (int64_t q : src)
+    if (q < -1 || q >= n_send) return fail(ctx, SBX_EINVAL, "contribution row out of range");
+  if (int rc = upload(ctx, &ctx->d_halo_send, snd)) return rc;
+  if (int rc = upload(ctx, &ctx->d_halo_cut, cut)) return rc;
+  if (int rc = upload(ctx, &ctx->d_halo_ptr, ptr)) return rc;
+  if (int rc = upload(ctx, &ctx->d_halo_src, src)) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->halo_n_send = n_send;
+  ctx->halo_n_cut = n_cut;
+  return SBX_OK;
+}
+
+int sbx_halo_pack(sbx_ctx *ctx, void *send_buf) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
+  if (ctx->halo_n_send > 0 && !is_device_ptr(send_buf))
+    return fail(ctx, SBX_EINVAL, "send_buf must be device memory");
+  CK(sbx::launch_halo_pack(ctx, send_buf, ctx->stream));
+  return SBX_OK;
+}
+
+int sbx_halo_sum(sbx_ctx *ctx, const void *recv_buf) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
+  if (ctx->halo_n_send > 0 && !is_device_ptr(recv_buf))
+    return fail(ctx, SBX_EINVAL, "recv_buf must be device memory");
+  CK(sbx::launch_halo_sum(ctx, recv_buf, ctx->stream));
+  return SBX_OK;
+}
+
+int sbx_share_state(sbx_ctx *ctx, sbx_ctx *owner) {
+  if (!ctx || !owner || ctx == owner) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (!ctx->have_mesh || !owner->have_mesh)
+    return fail(ctx, SBX_ESTATE, "both contexts need a mesh");
+  if (owner->state_owner) return fail(ctx, SBX_EINVAL, "the owner shares another context's state");
+  if (ctx->state_owner || ctx->n_guests) return fail(ctx, SBX_ESTATE, "state already shared");
+  if (ctx->device != owner->device || ctx->stream != owner->stream)
+    return fail(ctx, SBX_EINVAL, "both contexts must use one device and one stream");
+  if (ctx->N != owner->N || ctx->B != owner->B || ctx->prec != owner->prec)
+    return fail(ctx, SBX_EINVAL, "node count, load cases and precision must match");
+  CK(cudaStreamSynchronize(ctx->stream));
+  drop_graph(ctx);
+  dfree(ctx->d_u[0]); dfree(ctx->d_u[1]); dfree(ctx->d_f); dfree(ctx->d_pair);
+  ctx->d_u[0] = owner->d_u[0];
+  ctx->d_u[1] = owner->d_u[1];
+  ctx->d_f = owner->d_f;
+  ctx->d_pair = owner->d_pair;
+  ctx->state_owner = owner;
+  owner->n_guests += 1;
+  ctx->f_dirty = ctx->f_pending = false;
+  return SBX_OK;
+}
+
+int sbx_classify_cells(sbx_ctx *ctx, int64_t n_cells, const int32_t *slot_node,
+                       const int32_t *mask, int32_t *masters, int32_t *n_masters,
+                       int32_t *cell_pattern, uint8_t *cell_sym, int64_t *cell_ptr,
+                       int32_t *cell_nodes, int64_t *order, int64_t *pat_start, int32_t *conn) {
+  if (!ctx) return SBX_EINVAL;
+  if (int rc = set_device(ctx)) return rc;
+  ctx->err.clear();
+  if (n_cells < 1 || n_cells > ((int64_t)1 << 40))
+    return fail(ctx, SBX_EINVAL, "n_cells out of range");
+  if (!masters || !n_masters || !pat_start) return fail(ctx, SBX_EINVAL, "null host output");
+  const void *dev[] = {slot_node, mask, cell_pattern, cell_sym, cell_ptr, cell_nodes, order, conn};
+  for (const void *p : dev)
+    if (!is_device_ptr(p)) return fail(ctx, SBX_EINVAL, "per-cell arrays must be device memory");
+  cudaStream_t s = ctx->stream;
+  const int grid = ctx->n_sm * 8;
+  const int64_t nb = (n_cells + 1023) / 1024;
+  int32_t *table = nullptr, *used = nullptr, *pid = nullptr, *bad = nullptr;
+  int64_t *work = nullptr, *total = nullptr, *cnt = nullptr, *dstart = nullptr, *dcoff = nullptr;
+  auto release = [&]() {
+    dfree(table); dfree(used); dfree(pid); dfree(bad); dfree(work); dfree(total); dfree(cnt);
+    dfree(dstart); dfree(dcoff);
+  };
+  int rc = SBX_OK;
+  if (!rc) rc = dalloc(ctx, &table, 4096);
+  if (!rc) rc = dalloc(ctx, &used, 4096);
+  if (!rc) rc = dalloc(ctx, &pid, 4096);
+  if (!rc) rc = dalloc(ctx, &bad, 1);
+  if (!rc) rc = dalloc(ctx, &work, (size_t)std::max<int64_t>(nb, 1) * 145 + 2);
+  if (!rc) rc = dalloc(ctx, &total, 1);
+  if (rc) {
+    release();
+    return rc;
+  }
+  auto go = [&]() -> int {
+    CK(cudaMemsetAsync(used, 0, 4096 * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
+    CK(sbx::setup_mask_table(table, s));
+    CK(sbx::setup_flag_masters(n_cells, mask, table, used, grid, s));
+    std::vector<int32_t> hu(4096), hp(4096, -1);
+    CK(cudaMemcpyAsync(hu.data(), used, 4096 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int P = 0;
+    for (int q = 0; q < 4096; ++q)
+      if (hu[q]) {
+        masters[P] = q;
+        hp[q] = P++;
+      }
+    if (P > 144) return fail(ctx, SBX_EINVAL, "more than 144 master patterns");
+    *n_masters = P;
+    CK(cudaMemcpyAsync(pid, hp.data(), 4096 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(cell_ptr + n_cells, 0, sizeof(int64_t), s));
+    CK(sbx::setup_classify(n_cells, mask, table, pid, cell_pattern, cell_sym, cell_ptr, grid, s));
+    CK(sbx::setup_scan(n_cells + 1, cell_ptr, work, total, s));
+    CK(sbx::setup_cell_nodes(n_cells, slot_node, mask, table, cell_ptr, cell_nodes, bad, grid, s));
+    // stable sort by pattern: counts per (pattern, block), scanned pattern-major
+    if (int r = dalloc(ctx, &cnt, (size_t)P * nb + 1)) return r;
+    CK(sbx::setup_sort_count(n_cells, P, cell_pattern, cnt, s));
+    CK(sbx::setup_scan((int64_t)P * nb, cnt, work, total, s));
+    CK(sbx::setup_sort_scatter(n_cells, P, cell_pattern, cnt, order, s));
+    std::vector<int64_t> st(P + 1);
+    for (int p = 0; p < P; ++p)
+      CK(cudaMemcpyAsync(&st[p], cnt + (int64_t)p * nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    int32_t nbad = 0;
+    CK(cudaMemcpyAsync(&nbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (nbad) return fail(ctx, SBX_EINVAL, "a cell lacks a node its pattern needs");
+    st[P] = n_cells;
+    std::vector<int64_t> coff(P + 1, 0);
+    for (int p = 0; p <= P; ++p) pat_start[p] = st[p];
+    // node counts per pattern from the scanned pointers: n_p = ptr[e + 1] - ptr[e]
+    // of any cell e of the pattern (the first sorted one)
+    for (int p = 0; p < P; ++p) {
+      const int64_t Cp = st[p + 1] - st[p];
+      int64_t e = 0, a = 0, b = 0;
+      CK(cudaMemcpyAsync(&e, order + st[p], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      CK(cudaMemcpyAsync(&a, cell_ptr + e, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&b, cell_ptr + e + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      coff[p + 1] = coff[p] + (b - a) * Cp;
+    }
+    if (int r = upload(ctx, &dstart, st)) return r;
+    if (int r = upload(ctx, &dcoff, coff)) return r;
+    CK(sbx::setup_conn(n_cells, order, cell_pattern, dstart, dcoff, cell_ptr, cell_nodes, conn,
+                       grid, s));
+    CK(cudaStreamSynchronize(s));
+    return SBX_OK;
+  };
+  rc = go();
+  release();
+  return rc;
+}
+
 int sbx_set_launch(sbx_ctx *ctx, int what, int value) {
   if (!ctx) return SBX_EINVAL;
   ctx->err.clear();
@@ -1128,8 +1348,34 @@ int sbx_set_launch(sbx_ctx *ctx, int what, int value) {
       ctx->walsh_ctas = value;
       return SBX_OK;
     default:
-      return fail(ctx, SBX_EINVAL, "unknown launch parameter");
+      break;
   }
+  const bool cells = what >= SBX_LAUNCH_BATCH_TILE_CELLS && what < SBX_LAUNCH_BATCH_TILE_CELLS + 3;
+  const bool kb = what >= SBX_LAUNCH_BATCH_SMEM_KB && what < SBX_LAUNCH_BATCH_SMEM_KB + 3;
+  if (!cells && !kb) return fail(ctx, SBX_EINVAL, "unknown launch parameter");
+  if (cells && (value < 1 || value > 64)) return fail(ctx, SBX_EINVAL, "cells per tile: 1 .. 64");
+  if (kb && (value < 16 || value > 227)) return fail(ctx, SBX_EINVAL, "shared memory: 16 .. 227 KB");
+  const int c = what - (cells ? SBX_LAUNCH_BATCH_TILE_CELLS : SBX_LAUNCH_BATCH_SMEM_KB);
+  int &slot = cells ? ctx->b_tile_cells[c] : ctx->b_smem_kb[c];
+  if (slot == value) return SBX_OK;
+  const int old = slot;
+  slot = value;
+  if (!ctx->have_mesh || ctx->B == 1) return SBX_OK;
+  // rebuild the batched tiles with the new shape
+  if (int rc = set_device(ctx)) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  drop_graph(ctx);
+  std::string e;
+  const int rc = sbx::batch_setup(ctx, ctx->hb_conn, ctx->hb_conn_off, ctx->hb_cnt, ctx->hb_sym,
+                                  ctx->hb_scale, ctx->hb_start, e);
+  if (rc) {
+    slot = old;
+    std::string e2;
+    sbx::batch_setup(ctx, ctx->hb_conn, ctx->hb_conn_off, ctx->hb_cnt, ctx->hb_sym, ctx->hb_scale,
+                     ctx->hb_start, e2);
+    return fail(ctx, rc, e);
+  }
+  return SBX_OK;
 }
 
 int sbx_get_launch(sbx_ctx *ctx, int what, int *value) {
@@ -1142,8 +1388,17 @@ int sbx_get_launch(sbx_ctx *ctx, int what, int *value) {
       *value = ctx->walsh_ctas;
       return SBX_OK;
     default:
-      return fail(ctx, SBX_EINVAL, "unknown launch parameter");
+      break;
   }
+  if (what >= SBX_LAUNCH_BATCH_TILE_CELLS && what < SBX_LAUNCH_BATCH_TILE_CELLS + 3) {
+    *value = ctx->b_tile_cells[what - SBX_LAUNCH_BATCH_TILE_CELLS];
+    return SBX_OK;
+  }
+  if (what >= SBX_LAUNCH_BATCH_SMEM_KB && what < SBX_LAUNCH_BATCH_SMEM_KB + 3) {
+    *value = ctx->b_smem_kb[what - SBX_LAUNCH_BATCH_SMEM_KB];
+    return SBX_OK;
+  }
+  return fail(ctx, SBX_EINVAL, "unknown launch parameter");
 }
 
 int sbx_set_receivers(sbx_ctx *ctx, int64_t n_rec, const int64_t *rec_idx, int64_t max_steps) {
@@ -1256,6 +1511,7 @@ int sbx_set_step(sbx_ctx *ctx, int64_t n) {
 
 int read_field(sbx_ctx *ctx, int which, double *out, int64_t len) {
   if (!ctx) return SBX_EINVAL;
+  if (ctx->state_owner) return fail(ctx, SBX_ESTATE, "this context shares another context's state: only sbx_force applies");
   if (int rc = set_device(ctx)) return rc;
   ctx->err.clear();
   if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");
@@ -1284,6 +1540,7 @@ int read_field(sbx_ctx *ctx, int which, double *out, int64_t len) {
 
 int write_field(sbx_ctx *ctx, int which, const double *in, int64_t len) {
   if (!ctx) return SBX_EINVAL;
+  if (ctx->state_owner) return fail(ctx, SBX_ESTATE, "this context shares another context's state: only sbx_force applies");
   if (int rc = set_device(ctx)) return rc;
   ctx->err.clear();
   if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");

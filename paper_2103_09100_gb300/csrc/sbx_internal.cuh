@@ -165,7 +165,7 @@ struct sbx_ctx {
   int64_t *d_gt_boff = nullptr;
   int n_gt_tiles = 0;
   size_t gt_smem = 0;
-  bool hanging_tc = false;         // k_force_gen_tc instead of k_force_gen
+  bool hanging_tc = true;          // k_force_gen_tc (default) instead of k_force_gen
   int walsh_ctas = 0;              // Walsh-kernel CTAs per SM (0: automatic)
   // the 8-node tiles by the Walsh-basis SIMT kernel instead of the tensor
   // cores (sbx_set_mixed_kernel)
@@ -178,6 +178,15 @@ struct sbx_ctx {
   sbx::TcTile *d_b_tiles[3] = {};
   int n_b_tiles[3] = {}, b_nnmax[3] = {}, b_recmax[3] = {};
   size_t b_smem[3] = {};
+  // tile shape per class (sbx_set_launch): most cells per tile and the
+  // shared-memory budget per CTA in KB that bounds a tile's staging
+  int b_tile_cells[3] = {32, 32, 32};
+  int b_smem_kb[3] = {100, 100, 100};
+  // host copies of the sorted mesh, kept to rebuild the tiles
+  std::vector<int32_t> hb_conn;
+  std::vector<int64_t> hb_conn_off, hb_cnt, hb_start;
+  std::vector<uint8_t> hb_sym;
+  std::vector<double> hb_scale;
 
   // receiver time history (sbx_set_receivers): hist[row][n_rec], row = step
   // index - rec_step0 - 1 of the step just taken, rows < rec_cap
@@ -192,6 +201,15 @@ struct sbx_ctx {
   int32_t *d_load_kind = nullptr;
 
   sbx::GraphCache graph;
+
+  // node-cut interface sum with the neighbours (sbx_halo_plan)
+  int64_t halo_n_send = 0, halo_n_cut = 0, halo_n_recv_rows = 0;
+  int64_t *d_halo_send = nullptr, *d_halo_cut = nullptr, *d_halo_ptr = nullptr,
+          *d_halo_src = nullptr;
+  // sbx_share_state: this context steps nothing itself; its force kernels
+  // read the owner's state and add into the owner's accumulator
+  sbx_ctx *state_owner = nullptr;
+  int n_guests = 0;
 
   sbx::MeshView view() const {
     return sbx::MeshView{ndof, B, d_pat_m, d_koff, d_conn, d_conn_off, d_pat_cstart,
@@ -243,11 +261,40 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
              const std::vector<uint8_t> &sym_sorted, const std::vector<double> &scale_sorted,
              std::string &err);
 cudaError_t prepare_tc_kernels();
+// tables of the tensor-core kernels for the other patterns (the marked ones)
+int gt_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<int64_t> &conn_off,
+             const std::vector<int64_t> &cnt, const std::vector<int64_t> &start,
+             const std::vector<uint8_t> &sym_sorted, const std::vector<double> &scale_sorted,
+             const std::vector<char> &use, std::string &err);
+// batched FP32 form: the cells of the gt tables on the tensor cores
+cudaError_t launch_force_batch_tc(const sbx_ctx *ctx, const float *pairs, float *f, double dt,
+                                  LoadTable L, cudaStream_t s);
 cudaError_t launch_wait_selftest(const sbx_ctx *ctx, uint32_t polls, int arrive, cudaStream_t s);
 // kernels_eigen.cu: k Lanczos steps (full reorthogonalisation) of
 // M^-1/2 K M^-1/2 from v0 (device, 3N); alpha, beta: device, k doubles
 int lanczos_run(sbx_ctx *ctx, int64_t k, const double *v0_dev, double *alpha_dev,
                 double *beta_dev, std::string &err);
+// kernels_halo.cu: rows of the force accumulator to the send buffer
+// (d_halo_send order) and the canonical sum of the cut nodes' partial forces
+cudaError_t launch_halo_pack(const sbx_ctx *ctx, void *out, cudaStream_t s);
+cudaError_t launch_halo_sum(const sbx_ctx *ctx, const void *recv, cudaStream_t s);
+// kernels_setup.cu: classification, node lists, sort and connectivity on the GPU
+cudaError_t setup_mask_table(int32_t *table, cudaStream_t s);
+cudaError_t setup_flag_masters(int64_t n, const int32_t *mask, const int32_t *table, int32_t *used,
+                               int grid, cudaStream_t s);
+cudaError_t setup_classify(int64_t n, const int32_t *mask, const int32_t *table,
+                           const int32_t *pid, int32_t *pat, uint8_t *sym, int64_t *cnt, int grid,
+                           cudaStream_t s);
+cudaError_t setup_scan(int64_t n, int64_t *x, int64_t *work, int64_t *total, cudaStream_t s);
+cudaError_t setup_cell_nodes(int64_t n, const int32_t *slot_node, const int32_t *mask,
+                             const int32_t *table, const int64_t *ptr, int32_t *nodes, int32_t *bad,
+                             int grid, cudaStream_t s);
+cudaError_t setup_sort_count(int64_t n, int P, const int32_t *pat, int64_t *cnt, cudaStream_t s);
+cudaError_t setup_sort_scatter(int64_t n, int P, const int32_t *pat, const int64_t *off,
+                               int64_t *order, cudaStream_t s);
+cudaError_t setup_conn(int64_t n, const int64_t *order, const int32_t *pat, const int64_t *pstart,
+                       const int64_t *coff, const int64_t *ptr, const int32_t *nodes,
+                       int32_t *conn, int grid, cudaStream_t s);
 // kernels_batch.cu
 int batch_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<int64_t> &conn_off,
                 const std::vector<int64_t> &cnt, const std::vector<uint8_t> &sym_sorted,

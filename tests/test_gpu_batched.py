@@ -28,9 +28,11 @@ def _with_sources(m, B, seed, t1_scale=4.0):
     return m
 
 
-def _compare(m, B, precision, n_steps, tol, threads=4):
+def _compare(m, B, precision, n_steps, tol, threads=4, hanging=None):
     P0 = cdm.make_problem(m, rhs=0)
     S = Solver.from_mesh(m, precision=precision, n_rhs=B, dt=P0.dt)
+    if hanging is not None:
+        L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_HANGING_KERNEL, hanging)
     S.initial()
     S.step(n_steps)
     g = S.field(L.SBX_U_N).reshape(-1, B)
@@ -53,10 +55,14 @@ def test_batched_fp64_tiny():
     print("batched fp64 tiny: max rel error over 32 cases %.3e" % w)
 
 
-def test_batched_fp32_corner_cube_1000_steps():
+@pytest.mark.parametrize("hname, hanging", [("tensor cores", L.SBX_HANGING_TENSOR),
+                                            ("FP32 SIMT", L.SBX_HANGING_SIMT)])
+def test_batched_fp32_corner_cube_1000_steps(hname, hanging):
+    # the hanging-node patterns on the tensor cores (the default) or FP32 SIMT
     m = _with_sources(og.config_corner_cube(), 32, 7, t1_scale=10.0)
-    w = _compare(m, 32, "fp32", 1000, 1e-5)
-    print("batched fp32 corner cube, 1000 steps: max rel error over 32 cases %.3e" % w)
+    w = _compare(m, 32, "fp32", 1000, 1e-5, hanging=hanging)
+    print("batched fp32 corner cube, hanging patterns on %s, 1000 steps: max rel error over "
+          "32 cases %.3e" % (hname, w))
 
 
 def test_batched_64_cases_and_initial_field():

@@ -1,7 +1,7 @@
-"""The mixed form with the hanging-node patterns on the tensor cores
-(sbx_set_launch(SBX_LAUNCH_HANGING_KERNEL, SBX_HANGING_TENSOR): tiles of up
+"""The mixed form's two kernels for the hanging-node patterns against the
+FP64 oracle: the tensor cores (SBX_HANGING_TENSOR, the default: tiles of up
 to 128 cells of one pattern, TF32 x 3 with FP32 accumulation in tensor
-memory) against the FP64 oracle.  Errors by ``parity.rel`` (the larger of
+memory) and FP32 SIMT (SBX_HANGING_SIMT, sbx_set_launch).  Errors by ``parity.rel`` (the larger of
 the relative L2 and the element-wise error); bar 1e-5 as for every
 FP32-contraction form."""
 import numpy as np
@@ -21,12 +21,17 @@ def _built():
     L.load()
 
 
-def solver(m, regular=L.SBX_MIXED_WALSH, **kw):
+def solver(m, regular=L.SBX_MIXED_WALSH, hanging=L.SBX_HANGING_TENSOR, **kw):
     S = Solver.from_mesh(m, precision="mixed", **kw)
-    L.sbx_set_mixed_kernel(S.ctx, regular)
-    L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_HANGING_KERNEL, L.SBX_HANGING_TENSOR)
+    # the tensor-core kernel is the library's default for these patterns
     assert L.sbx_get_launch(S.ctx, L.SBX_LAUNCH_HANGING_KERNEL) == L.SBX_HANGING_TENSOR
+    L.sbx_set_mixed_kernel(S.ctx, regular)
+    L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_HANGING_KERNEL, hanging)
+    assert L.sbx_get_launch(S.ctx, L.SBX_LAUNCH_HANGING_KERNEL) == hanging
     return S
+
+
+HANGING = [("tensor", L.SBX_HANGING_TENSOR), ("simt", L.SBX_HANGING_SIMT)]
 
 
 @pytest.mark.parametrize("seed", [0, 1, 3, 4])
@@ -50,12 +55,13 @@ def test_force_and_steps_tiny(seed):
     assert rel(S.field(L.SBX_U_N), u) < 1e-5
 
 
+@pytest.mark.parametrize("hname, hanging", HANGING)
 @pytest.mark.parametrize("regular", [L.SBX_MIXED_WALSH, L.SBX_MIXED_TENSOR])
-def test_corner_cube_2000_steps(regular):
+def test_corner_cube_2000_steps(regular, hname, hanging):
     # 30 patterns up to 26 nodes (78 DOF: the widest tile, N = 80)
     m = og.config_corner_cube()
     P = cdm.make_problem(m)
-    S = solver(m, regular, dt=P.dt)
+    S = solver(m, regular, hanging, dt=P.dt)
     S.initial()
     u, up = cdm.initial_state(P)
     worst = 0.0
@@ -63,15 +69,16 @@ def test_corner_cube_2000_steps(regular):
         S.step(500)
         u, up, _, _ = cdm.run(P, 500, u, up, n0=500 * k, threads=16)
         worst = max(worst, rel(S.field(L.SBX_U_N), u))
-    print("corner cube, hanging patterns on tensor cores, 2000 steps: %.3e" % worst)
+    print("corner cube, hanging patterns on %s, 2000 steps: %.3e" % (hname, worst))
     assert worst < 1e-5
 
 
-def test_cavity_force_and_200_steps():
+@pytest.mark.parametrize("hname, hanging", HANGING)
+def test_cavity_force_and_200_steps(hname, hanging):
     # full size: 30k hanging cells in 26 patterns, the benchmark's launch shape
     m = og.config_cavity_cube()
     P = cdm.make_problem(m)
-    S = solver(m, dt=P.dt)
+    S = solver(m, hanging=hanging, dt=P.dt)
     u0 = np.random.default_rng(3).standard_normal(m.n_dof) * 1e-3
     u0[P.fixed] = 0
     S.initial(u0)
@@ -83,7 +90,7 @@ def test_cavity_force_and_200_steps():
     u, up = cdm.initial_state(P, u0)
     u, _, _, _ = cdm.run(P, 200, u, up, threads=16)
     e = rel(S.field(L.SBX_U_N), u)
-    print("cavity cube, hanging patterns on tensor cores: force %.3e, 200 steps %.3e" % (ef, e))
+    print("cavity cube, hanging patterns on %s: force %.3e, 200 steps %.3e" % (hname, ef, e))
     assert ef < 1e-5 and e < 1e-5
 
 

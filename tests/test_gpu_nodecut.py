@@ -78,3 +78,93 @@ def test_split_step_equals_step_n():
     L.sbx_force(B.ctx, B.dt)
     with pytest.raises(L.SbxError):
         L.sbx_force(B.ctx, B.dt)
+
+
+def _run_neighbours(m, n_parts, precision, n_steps, overlap=True, u0=None):
+    parts = partition(m.slot_node, n_parts, fixed_nodes=m.fixed_nodes, sources=m.sources,
+                      weight=((m.slot_node >= 0).sum(1) ** 2))
+    eng = [nodecut.NodeCutSolver(p, m.mask, m.h, m.E, m.rho, m.nu, precision=precision,
+                                 overlap=overlap) for p in parts]
+    assert all(e.G is not None for e in eng) == overlap
+    dt = nodecut.setup_together(eng, 0.5, u0=u0)
+    nodecut.step_neighbours_together(eng, n_steps)
+    out = [(e.part.nodes, e.part.cut_local, e.field(L.SBX_U_N).reshape(-1, 3)) for e in eng]
+    nb = [len(e.plan.neighbours) for e in eng]
+    for e in eng:
+        e.close()
+    return dt, out, nb
+
+
+@pytest.mark.parametrize("n_parts", [3, 4])
+def test_neighbour_exchange_with_overlap_fp64(n_parts):
+    # interface cells (owner context) and interior cells (guest on the same
+    # state), shared rows packed and summed by the library's kernels
+    m = og.config_corner_cube()
+    m.E = np.exp(0.3 * np.random.default_rng(4).standard_normal(m.n_cells))
+    u0 = np.random.default_rng(5).standard_normal(m.n_dof) * 1e-3
+    dt, out, nb = _run_neighbours(m, n_parts, "fp64", 200, u0=u0)
+    if n_parts == 4:
+        assert max(nb) >= 3
+    P = cdm.make_problem(m, dt=dt)
+    u, up = cdm.initial_state(P, u0)
+    u, _, _, _ = cdm.run(P, 200, u, up, threads=4)
+    ug = u.reshape(-1, 3)
+    seen = {}
+    for nodes, cut, ul in out:
+        assert np.abs(ul - ug[nodes]).max() <= 1e-11 * np.abs(ug).max()
+        for v in cut:   # identical histories of a cut node on all its parts
+            g = int(nodes[v])
+            if g in seen:
+                assert np.array_equal(seen[g], ul[v])
+            else:
+                seen[g] = ul[v].copy()
+
+
+def test_neighbour_exchange_with_overlap_mixed_receiver_cube():
+    m = og.config_receiver_cube()
+    dt, out, _ = _run_neighbours(m, 3, "mixed", 300)
+    P = cdm.make_problem(m, dt=dt)
+    u, up = cdm.initial_state(P)
+    u, _, _, _ = cdm.run(P, 300, u, up, threads=16)
+    ug = u.reshape(-1, 3)
+    num = sum(float(np.sum((ul - ug[nodes]) ** 2)) for nodes, _, ul in out)
+    den = sum(float(np.sum(ug[nodes] ** 2)) for nodes, _, _ in out)
+    mx = max(float(np.abs(ul - ug[nodes]).max()) for nodes, _, ul in out) / np.abs(ug).max()
+    e = max((num / den) ** 0.5, mx)
+    print("node-cut mixed, 3 parts, neighbour exchange with overlap, 300 steps: %.3e" % e)
+    assert e < 1e-5
+
+
+def test_shared_state_rules():
+    from paper_2103_09100_gb300 import Solver
+    import torch
+    m = og.config_corner_cube()
+    m.sources = []
+    st = torch.cuda.Stream()
+    A = Solver.from_mesh(m, precision="fp64", stream=st.cuda_stream)
+    B = Solver.from_mesh(m, precision="fp64", stream=st.cuda_stream, dt=A.dt)
+    C = Solver.from_mesh(m, precision="fp64", dt=A.dt)   # its own stream
+    with pytest.raises(L.SbxError):
+        L.sbx_share_state(C.ctx, A.ctx)
+    L.sbx_share_state(B.ctx, A.ctx)
+    for call in (lambda: B.step(1), lambda: B.field(), lambda: L.sbx_update(B.ctx, B.dt)):
+        with pytest.raises(L.SbxError) as e:
+            call()
+        assert e.value.code == L.SBX_ESTATE
+    with pytest.raises(L.SbxError) as e:
+        L.sbx_destroy(A.ctx)
+    assert e.value.code == L.SBX_ESTATE
+    # the guest adds the same cells' forces into the owner's accumulator:
+    # owner + guest = twice the owner's force
+    u0 = np.random.default_rng(1).standard_normal(m.n_dof)
+    A.initial(u0)
+    L.sbx_force(A.ctx, A.dt)
+    f1 = L.read_field(A.ctx, L.SBX_F_INT, np.empty(m.n_dof)).copy()
+    A.initial(u0)
+    L.sbx_force(A.ctx, A.dt)
+    L.sbx_force(B.ctx, A.dt)
+    f2 = L.read_field(A.ctx, L.SBX_F_INT, np.empty(m.n_dof))
+    assert np.abs(f2 - 2 * f1).max() <= 1e-12 * np.abs(f1).max()
+    B.close()
+    C.close()
+    A.close()

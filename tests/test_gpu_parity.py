@@ -112,6 +112,29 @@ def test_triangle_and_sine_burst_loads(wave, ncyc, prec, tol):
     assert worst < tol
 
 
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_line_loads(prec, tol):
+    # Sec. 5.5's panel loads: a line load P_x along y = 1/2 and a line load
+    # P_y along x = 1/4 on the top face; the library gets the product's
+    # nodal forces (loads.line_load), the oracle its own (line_load_forces)
+    from paper_2103_09100_gb300 import loads
+    m = og.config_corner_cube()
+    t1 = og.ricker_t1_for_mesh(m, 4.0)
+    lines = [(((0, 0.5, 1), (1, 0.5, 1)), (1.0, 0.0, 0.0), 2.0),
+             (((0.25, 0, 1), (0.25, 1, 1)), (0.0, 1.0, 0.0), -1.0)]
+    m.sources = sum([loads.line_load(m.node_xyz, a, b, d, q, t1) for (a, b), d, q in lines], [])
+    S = _solver(m, cdm.make_problem(m), precision=prec)
+    src = []
+    for (a, b), d, q in lines:
+        for node, force in sorted(cdm.line_load_forces(m, a, b, q).items()):
+            src.append({"node": node, "dir": list(d), "t1": t1, "P0": force, "wavelet": "ricker"})
+    P = cdm.make_problem(m, sources=src)
+    assert len(P.load_dof) == len(m.sources)
+    worst, _ = _run_pair(m, P, S, 500, chunk=125)
+    print("corner cube, line loads, %s: max rel error over 500 steps %.3e" % (prec, worst))
+    assert worst < tol
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 65, 97])
 def test_step_counts_and_graph_replay(n):
     m = _tiny(1)

@@ -17,7 +17,8 @@ torch = pytest.importorskip("torch")
 import octree_gen as og
 from oracle import assembly, cdm
 from paper_2103_09100_gb300 import nodecut
-from paper_2103_09100_gb300.partition import HaloExchange, partition, split_ranges
+from paper_2103_09100_gb300.partition import (HaloExchange, halo_pack_host, halo_plan,
+                                               halo_sum_host, partition, split_ranges)
 
 
 def sub_mesh(mesh, part):
@@ -93,6 +94,51 @@ class OracleEngine:
         self.up, self.u = self.u, un
         self.n += 1
         self.pending = False
+
+
+class OracleNeighbourEngine(OracleEngine):
+    """The oracle engine with the neighbour-only exchange: the part's cells
+    split into interface cells (touching a cut node) and interior cells,
+    the shared rows packed, the canonical sum on the host."""
+
+    def __init__(self, mesh, part, alpha=0.0):
+        super().__init__(mesh, part, alpha)
+        self.torch = torch
+        self.plan = halo_plan(part)
+        self.recv = torch.zeros((max(1, self.plan.n_rows), 3), dtype=torch.float64)
+        sn = part.slot_node
+        cut = np.zeros(part.n_nodes, bool)
+        cut[part.cut_local] = True
+        self.inter = (cut[np.maximum(sn, 0)] & (sn >= 0)).any(1)
+
+    def _problem(self, sel):
+        m = copy.copy(self.sub)
+        m.level, m.anchor, m.h, m.mask = (a[sel] for a in (m.level, m.anchor, m.h, m.mask))
+        m.E, m.rho, m.slot_node = m.E[sel], m.rho[sel], m.slot_node[sel]
+        with np.errstate(divide="ignore"):
+            return cdm.make_problem(m, dt=self.dt, alpha=self.alpha)
+
+    def set_dt(self, dt):
+        super().set_dt(dt)
+        self.P_I = self._problem(np.nonzero(self.inter)[0])
+        self.P_R = self._problem(np.nonzero(~self.inter)[0]) if (~self.inter).any() else None
+
+    def force_interface(self):
+        if self.pending:
+            return False
+        self.f = cdm.apply_K(self.P_I, self.u) - cdm.external_force(self.P, self.n)
+        self.pending = True
+        return True
+
+    def force_interior(self):
+        if self.P_R is not None:
+            self.f = self.f + cdm.apply_K(self.P_R, self.u)
+
+    def pack(self):
+        return torch.from_numpy(np.ascontiguousarray(halo_pack_host(self.plan, self.f.reshape(-1, 3))))
+
+    def sum(self, recv):
+        halo_sum_host(self.plan, self.f.reshape(-1, 3), recv.numpy())
 
 
 def _mesh():
@@ -251,3 +297,109 @@ def test_gloo_rank_leaving_is_detected():
         s1 = open(os.path.join(d, "r1.txt")).read()
     assert s1 == "left"
     assert s0.startswith("detected"), s0
+
+
+@pytest.mark.parametrize("P", [3, 4, 6])
+def test_halo_plan_neighbour_lists(P):
+    m = _mesh()
+    parts = partition(m.slot_node, P)
+    byr = {p.rank: p for p in parts}
+    n_nb = []
+    for p in parts:
+        pl = halo_plan(p)
+        n_nb.append(len(pl.neighbours))
+        for q, loc in p.shared.items():
+            other = byr[q]
+            # the shared nodes, the same on both sides and in the same order
+            assert np.array_equal(p.nodes[loc], other.nodes[other.shared[p.rank]])
+            assert np.array_equal(p.nodes[loc], np.intersect1d(p.nodes, other.nodes))
+        # each cut node: one contribution per holding part, own one once
+        for j, v in enumerate(pl.cut_nodes):
+            src = pl.contrib_src[pl.contrib_ptr[j]:pl.contrib_ptr[j + 1]]
+            assert len(src) == len(p.holders[j]) >= 2
+            assert (src < 0).sum() == 1
+            assert list(p.holders[j]) == sorted(p.holders[j])
+    # the mesh gives every part of a 4+-part partition several neighbours
+    if P >= 4:
+        assert max(n_nb) >= 3
+
+
+@pytest.mark.parametrize("P", [3, 5])
+def test_neighbour_sum_gives_global_force_on_every_holder(P):
+    m = _mesh()
+    Pg = cdm.make_problem(m)
+    u = np.random.default_rng(1).standard_normal(m.n_dof)
+    fg = cdm.apply_K(Pg, u).reshape(-1, 3)
+    parts = partition(m.slot_node, P)
+    plans = [halo_plan(p) for p in parts]
+    fl = [cdm.apply_K(cdm.make_problem(sub_mesh(m, p)), u.reshape(-1, 3)[p.nodes].ravel()).reshape(-1, 3)
+          for p in parts]
+    sends = [halo_pack_host(pl, f) for pl, f in zip(plans, fl)]
+    byr = {p.rank: (p, pl, snd) for p, pl, snd in zip(parts, plans, sends)}
+    for p, pl, f in zip(parts, plans, fl):
+        recv = np.zeros_like(sends[p.rank])
+        for i, q in enumerate(pl.neighbours):
+            op, opl, osnd = byr[int(q)]
+            j = int(np.nonzero(opl.neighbours == p.rank)[0][0])
+            recv[pl.send_ptr[i]:pl.send_ptr[i + 1]] = osnd[opl.send_ptr[j]:opl.send_ptr[j + 1]]
+        halo_sum_host(pl, f, recv)
+        assert np.abs(f - fg[p.nodes]).max() <= 1e-12 * np.abs(fg).max()
+    # every holder of a cut node computed the same sum, bit for bit
+    seen = {}
+    for p, f in zip(parts, fl):
+        for v in p.cut_local:
+            g = int(p.nodes[v])
+            if g in seen:
+                assert np.array_equal(seen[g], f[v])
+            else:
+                seen[g] = f[v].copy()
+
+
+def _rank_neighbours(rank, world, port, out_dir, n_steps):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank,
+                            world_size=world)
+    try:
+        m = _mesh()
+        parts = partition(m.slot_node, world, fixed_nodes=m.fixed_nodes, sources=m.sources)
+        e = OracleNeighbourEngine(m, parts[rank])
+        u0 = np.random.default_rng(2).standard_normal(m.n_dof) * 1e-3
+        dt = nodecut.setup_distributed(e, 0.5, u0=u0)
+        times = {}
+        nodecut.step_neighbours(e, n_steps, times=times)
+        np.savez(os.path.join(out_dir, "r%d.npz" % rank), u=e.u, nodes=e.part.nodes, dt=dt,
+                 cut=e.part.nodes[e.part.cut_local], nb=e.plan.neighbours,
+                 n_inter=int((~e.inter).sum()), t_C=times["t_C"], t_W=times["t_W"])
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_four_ranks_neighbour_exchange_equal_global_oracle():
+    mp = pytest.importorskip("torch.multiprocessing")
+    n_steps, world = 30, 4
+    with tempfile.TemporaryDirectory() as d:
+        mp.spawn(_rank_neighbours, args=(world, _free_port(), d, n_steps), nprocs=world, join=True)
+        res = [np.load(os.path.join(d, "r%d.npz" % r)) for r in range(world)]
+    m = _mesh()
+    dt = float(res[0]["dt"])
+    Pg = cdm.make_problem(m, dt=dt)
+    u0 = np.random.default_rng(2).standard_normal(m.n_dof) * 1e-3
+    u, up = cdm.initial_state(Pg, u0)
+    u, _, _, _ = cdm.run(Pg, n_steps, u, up)
+    ug = u.reshape(-1, 3)
+    assert max(len(r["nb"]) for r in res) >= 3          # a part with three neighbours
+    assert all(int(r["n_inter"]) > 0 for r in res)      # interior cells overlap the exchange
+    seen = {}
+    for r in res:
+        ul = r["u"].reshape(-1, 3)
+        assert float(r["dt"]) == dt
+        assert np.abs(ul - ug[r["nodes"]]).max() <= 1e-12 * np.abs(ug).max()
+        assert float(r["t_C"]) > 0.0 and float(r["t_W"]) > 0.0
+        # the cut nodes' histories are identical on every rank that holds them
+        pos = {int(g): i for i, g in enumerate(r["nodes"])}
+        for g in r["cut"]:
+            row = ul[pos[int(g)]]
+            if int(g) in seen:
+                assert np.array_equal(seen[int(g)], row)
+            else:
+                seen[int(g)] = row
