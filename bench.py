@@ -359,6 +359,8 @@ def main():
                          "TF32x3, the library's default; simt: FP32 FFMA)")
     ap.add_argument("--walsh-ctas", type=int, default=0,
                     help="mixed form: Walsh-kernel CTAs per SM (0: the library's choice)")
+    ap.add_argument("--hanging-ctas", type=int, default=None,
+                    help="mixed form: CTAs per SM of the tensor-core hanging-pattern kernel")
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
@@ -399,6 +401,8 @@ def main():
                          L.SBX_HANGING_TENSOR if args.hanging == "tensor" else L.SBX_HANGING_SIMT)
     if args.precision == "mixed":
         L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_WALSH_CTAS_PER_SM, args.walsh_ctas)
+        if args.hanging_ctas is not None:
+            L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_HANGING_CTAS_PER_SM, args.hanging_ctas)
     hanging_tc = (args.precision == "mixed" and
                   L.sbx_get_launch(S.ctx, L.SBX_LAUNCH_HANGING_KERNEL) == L.SBX_HANGING_TENSOR)
     S.initial()

@@ -440,7 +440,8 @@ int sbx_halo_sum(sbx_ctx *ctx, const void *recv_buf);
  * splits one part's cells in two, e.g. the cells on the interface and the
  * interior ones, so that the interface exchange can run while the interior
  * force is computed (the computation order of Sec. 4.2).  A guest's other
- * stepping calls fail with SBX_ESTATE; loads belong on the owner; the owner
+ * stepping calls and field reads fail with SBX_ESTATE (its own lumped mass,
+ * read_field(SBX_MASS), stays readable); loads belong on the owner; the owner
  * clears the accumulator in its sbx_update and is destroyed after its
  * guests (sbx_destroy of an owner with guests: SBX_ESTATE).
  *   Errors: SBX_EINVAL (sizes, devices or streams differ), SBX_ESTATE.
@@ -488,6 +489,8 @@ int sbx_classify_cells(sbx_ctx *ctx, int64_t n_cells, const int32_t *slot_node,
  *       or on FP32 SIMT (SBX_HANGING_SIMT).
  *   SBX_LAUNCH_WALSH_CTAS_PER_SM   mixed form: resident CTAs per SM of the
  *       Walsh-basis kernel, 1 .. 8, or 0 for the library's choice.
+ *   SBX_LAUNCH_HANGING_CTAS_PER_SM mixed form: CTAs per SM of the
+ *       tensor-core kernel of the hanging-node patterns, 1 (default) or 2.
  *   SBX_LAUNCH_BATCH_TILE_CELLS + c   batched form, pattern class c (0: up
  *       to 8 nodes, 1: up to 16, 2: more): most cells per tile, 1 .. 64
  *       (default 32).  A change rebuilds the class's tiles.
@@ -499,6 +502,7 @@ int sbx_classify_cells(sbx_ctx *ctx, int64_t n_cells, const int32_t *slot_node,
  */
 #define SBX_LAUNCH_HANGING_KERNEL     0
 #define SBX_LAUNCH_WALSH_CTAS_PER_SM  1
+#define SBX_LAUNCH_HANGING_CTAS_PER_SM 2
 #define SBX_LAUNCH_BATCH_TILE_CELLS   16
 #define SBX_LAUNCH_BATCH_SMEM_KB      20
 #define SBX_HANGING_SIMT   0

@@ -31,7 +31,7 @@ EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patte
            "sbx_lanczos", "sbx_set_mixed_kernel", "sbx_prepare_steps", "sbx_set_launch",
            "sbx_get_launch", "sbx_halo_plan", "sbx_halo_pack", "sbx_halo_sum", "sbx_share_state",
            "sbx_classify_cells"]
-SBX_LAUNCH_HANGING_KERNEL, SBX_LAUNCH_WALSH_CTAS_PER_SM = 0, 1
+SBX_LAUNCH_HANGING_KERNEL, SBX_LAUNCH_WALSH_CTAS_PER_SM, SBX_LAUNCH_HANGING_CTAS_PER_SM = 0, 1, 2
 SBX_LAUNCH_BATCH_TILE_CELLS, SBX_LAUNCH_BATCH_SMEM_KB = 16, 20
 SBX_HANGING_SIMT, SBX_HANGING_TENSOR = 0, 1
 SBX_LAYOUT_F64_DOF, SBX_LAYOUT_F32_NODE4, SBX_LAYOUT_F32_DOF = 0, 1, 2

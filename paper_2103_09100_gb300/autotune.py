@@ -17,7 +17,7 @@ Searched parameters (``sbx_set_launch``):
   most cells per tile and the shared-memory budget per CTA (which sets how
   many CTAs share an SM);
 * mixed form: the kernel for the hanging-node patterns (tensor cores or
-  FP32 SIMT) and the Walsh kernel's CTAs per SM.
+  FP32 SIMT), its CTAs per SM, and the Walsh kernel's CTAs per SM.
 """
 from __future__ import annotations
 
@@ -31,7 +31,8 @@ from . import _lib as L
 BATCH_CELLS = (8, 16, 32, 64)
 BATCH_SMEM_KB = (56, 72, 100, 150)
 MIXED_HANGING = (L.SBX_HANGING_TENSOR, L.SBX_HANGING_SIMT)
-MIXED_WALSH_CTAS = (0, 4, 5, 6)
+MIXED_WALSH_CTAS = (0, 3, 4, 5, 6)
+MIXED_HANGING_CTAS = (1, 2)
 
 
 def search_space(solver):
@@ -44,6 +45,7 @@ def search_space(solver):
         return space
     if solver.precision == "mixed":
         return [(L.SBX_LAUNCH_HANGING_KERNEL, MIXED_HANGING),
+                (L.SBX_LAUNCH_HANGING_CTAS_PER_SM, MIXED_HANGING_CTAS),
                 (L.SBX_LAUNCH_WALSH_CTAS_PER_SM, MIXED_WALSH_CTAS)]
     return []
 

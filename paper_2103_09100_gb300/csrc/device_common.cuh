@@ -109,6 +109,25 @@ __device__ __forceinline__ void st_hint(float4 *a, float4 v, uint64_t pol) {
                "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol)
                : "memory");
 }
+__device__ __forceinline__ double2 ld_nc_hint(const double2 *a, uint64_t pol) {
+  double2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+               : "=d"(v.x), "=d"(v.y)
+               : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double2 ld_hint(const double2 *a, uint64_t pol) {
+  double2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+               : "=d"(v.x), "=d"(v.y)
+               : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_hint(double2 *a, double2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(a), "d"(v.x), "d"(v.y),
+               "l"(pol)
+               : "memory");
+}
 __device__ __forceinline__ void st_hint(float2 *a, float2 v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y),
                "l"(pol)

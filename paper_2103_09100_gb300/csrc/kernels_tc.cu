@@ -465,8 +465,10 @@ struct WhtF {
 };
 
 struct WtLayout {
-  uint32_t stage[2], u_off, total;
+  uint32_t stage[2], u_off, d4, total;
 };
+// two stages (record, node pairs), then the tile's nodes as FP32
+// differences to its first node, float4 (x, y, z, unused) per node
 __host__ __device__ inline WtLayout wt_layout(int rec_max, int nn_max) {
   WtLayout L;
   uint32_t o = 128;   // 2 record mbarriers
@@ -474,6 +476,7 @@ __host__ __device__ inline WtLayout wt_layout(int rec_max, int nn_max) {
   const uint32_t st = a128(L.u_off + 24u * (uint32_t)nn_max);
   L.stage[0] = o; o += st;
   L.stage[1] = o; o += st;
+  L.d4 = o; o += a128(16u * (uint32_t)nn_max);
   L.total = o;
   return L;
 }
@@ -498,6 +501,7 @@ __global__ void __launch_bounds__(WT_THREADS, 6)
   extern __shared__ __align__(128) unsigned char smem[];
   const WtLayout SL = wt_layout(rec_max, nn_max);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [0], [1] records of stage 0, 1
+  float4 *D4 = reinterpret_cast<float4 *>(smem + SL.d4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x;
   const uint32_t mb_rec0 = tc::smem_addr(&mbar[0]);
@@ -561,6 +565,15 @@ __global__ void __launch_bounds__(WT_THREADS, 6)
     const Stage S = stage_view(stage_base(s), SL.u_off);
     const int ncell = S.hdr[1], nn = S.hdr[2];
     const bool brick = S.hdr[3] == 1;
+    // every node of the tile once: FP32 difference to the tile's first node
+    // from the (hi, lo) pairs (a constant shift of all a cell's corners
+    // leaves its force unchanged: K_p annihilates translations)
+    for (int q = tid; q < nn; q += WT_THREADS) {
+      float d0, d1, d2;
+      node_diff(S.u + 6 * q, S.u, d0, d1, d2);
+      D4[q] = make_float4(d0, d1, d2, 0.0f);
+    }
+    __syncthreads();
     // o[r][k]: component r at corner k = a + 2 b + 4 c of this cell's force
     float o[3][8];
     if (fc < ncell) {
@@ -575,9 +588,13 @@ __global__ void __launch_bounds__(WT_THREADS, 6)
 #pragma unroll
         for (int k = 0; k < 8; ++k) lk[k] = (w4[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
       }
-      const float *ref = S.u + 6 * lk[0];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) node_diff(S.u + 6 * lk[k], ref, o[0][k], o[1][k], o[2][k]);
+      for (int k = 0; k < 8; ++k) {
+        const float4 v = D4[lk[k]];
+        o[0][k] = v.x;
+        o[1][k] = v.y;
+        o[2][k] = v.z;
+      }
       wht8f(o[0]);
       wht8f(o[1]);
       wht8f(o[2]);
@@ -816,8 +833,7 @@ constexpr int GT_GROUPS = 4;        // 8-node groups: up to 32 >= 26 nodes
 constexpr uint32_t GT_COLS = 256;   // TMEM: D in 0..79, A from column 80 on
 constexpr uint32_t GT_COL_A = 80;   // chunk ks: hi at 80 + 16 ks, lo at 88 + 16 ks
 constexpr int GT_NPMAX = 80, GT_KPMAX = 80;
-constexpr uint32_t GT_B_OFF = 128;
-constexpr uint32_t GT_REC_OFF = GT_B_OFF + 2u * GT_NPMAX * GT_KPMAX * 4u;
+constexpr uint32_t GT_B_OFF = 128;   // B at 128, the record after the largest B of the mesh
 
 __host__ __device__ inline int gt_kp(int m) { return (m + 7) & ~7; }
 __host__ __device__ inline int gt_np(int m) { return (m + 15) & ~15; }
@@ -832,20 +848,24 @@ __host__ __device__ inline GtRec gt_rec_layout(int n) {
   R.bytes = R.ids + 128u * 4u * (uint32_t)n;
   return R;
 }
-__host__ __device__ inline uint32_t gt_smem_bytes(int n_max) {
-  return GT_REC_OFF + gt_rec_layout(n_max).bytes;
+__host__ __device__ inline uint32_t gt_rec_off(int b_floats_max) {
+  return GT_B_OFF + 4u * (uint32_t)b_floats_max;
+}
+__host__ __device__ inline uint32_t gt_smem_bytes(int n_max, int b_floats_max) {
+  return gt_rec_off(b_floats_max) + gt_rec_layout(n_max).bytes;
 }
 
 __global__ void __launch_bounds__(GT_THREADS, 1)
     k_force_gen_tc(const TcTile *__restrict__ tiles, int ntiles, const uint8_t *__restrict__ recs,
                    const float *__restrict__ Bg, const int64_t *__restrict__ boff,
                    const float *__restrict__ u, float *__restrict__ f4, LoadTable Ld,
-                   const int64_t *__restrict__ d_step, double dt, int32_t *flags) {
+                   const int64_t *__restrict__ d_step, double dt, int32_t *flags,
+                   uint32_t rec_off) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [0] record, [1] B, [2] MMA
   uint32_t *taddr_s = reinterpret_cast<uint32_t *>(smem + 32);
   float *Bs = reinterpret_cast<float *>(smem + GT_B_OFF);
-  unsigned char *rec = smem + GT_REC_OFF;
+  unsigned char *rec = smem + rec_off;
   const int tid = threadIdx.x, warp = tid >> 5, c = tid;
   const int G = gridDim.x;
   const uint32_t mb_rec = tc::smem_addr(&mbar[0]), mb_b = mb_rec + 8u, mb_mma = mb_rec + 16u;
@@ -1088,12 +1108,12 @@ __global__ void __launch_bounds__(BTC_THREADS, 2)
                      const uint8_t *__restrict__ recs, const float *__restrict__ Bg,
                      const int64_t *__restrict__ boff, const float2 *__restrict__ u,
                      float *__restrict__ f, int B, LoadTable Ld, const int64_t *__restrict__ d_step,
-                     double dt, int32_t *flags) {
+                     double dt, int32_t *flags, uint32_t rec_off) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [0] record, [1] B, [2] MMA
   uint32_t *taddr_s = reinterpret_cast<uint32_t *>(smem + 32);
   float *Bs = reinterpret_cast<float *>(smem + GT_B_OFF);
-  unsigned char *rec = smem + GT_REC_OFF;
+  unsigned char *rec = smem + rec_off;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x;
   const uint32_t mb_rec = tc::smem_addr(&mbar[0]), mb_b = mb_rec + 8u, mb_mma = mb_rec + 16u;
@@ -1340,12 +1360,13 @@ int gt_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   std::vector<int64_t> boff(P + 1, 0);
   std::vector<uint8_t> recs;
   std::vector<std::pair<int64_t, TcTile>> tl;   // (cost, tile)
-  int nmax = 1;
+  int nmax = 1, bmax = 0;
   for (int p = 0; p < P; ++p) {
     boff[p] = (int64_t)Bgt.size();
     if (!use[p] || cnt[p] == 0) continue;
     const int np = ctx->pat_nodes[p], m = 3 * np;
     const int KP = gt_kp(m), NP = gt_np(m), NKc = KP / 4;
+    bmax = std::max(bmax, 2 * NP * KP);
     Bgt.resize(Bgt.size() + 2 * (size_t)NP * KP, 0.0f);
     float *Bh = Bgt.data() + boff[p], *Bl = Bh + (size_t)NP * KP;
     for (int i = 0; i < m; ++i)
@@ -1413,7 +1434,8 @@ int gt_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
   if (int rc = up(&ctx->d_gt_rec, recs)) return rc;
   if (int rc = up(&ctx->d_gt_tiles, tiles)) return rc;
   ctx->n_gt_tiles = (int)tiles.size();
-  ctx->gt_smem = gt_smem_bytes(nmax);
+  ctx->gt_rec_off = gt_rec_off(bmax);
+  ctx->gt_smem = gt_smem_bytes(nmax, bmax);
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     err = "stream synchronisation failed";
     return SBX_ECUDA;
@@ -1686,10 +1708,10 @@ cudaError_t prepare_tc_kernels() {
   e = cudaFuncSetAttribute(k_force_wht32, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_force_gen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)gt_smem_bytes(26));
+                           (int)gt_smem_bytes(26, 2 * GT_NPMAX * GT_KPMAX));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_force_batch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)gt_smem_bytes(26));
+                           (int)gt_smem_bytes(26, 2 * GT_NPMAX * GT_KPMAX));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_force_gen, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)gen_smem(78));
@@ -1702,7 +1724,8 @@ cudaError_t launch_force_batch_tc(const sbx_ctx *ctx, const float *pairs, float 
   const int grid = std::max(1, std::min(items, 2 * ctx->n_sm));
   k_force_batch_tc<<<grid, BTC_THREADS, ctx->gt_smem, s>>>(
       ctx->d_gt_tiles, ctx->n_gt_tiles, nchunks, ctx->d_gt_rec, ctx->d_gt_B, ctx->d_gt_boff,
-      reinterpret_cast<const float2 *>(pairs), f, ctx->B, L, ctx->d_step, dt, ctx->d_flags);
+      reinterpret_cast<const float2 *>(pairs), f, ctx->B, L, ctx->d_step, dt, ctx->d_flags,
+      ctx->gt_rec_off);
   return cudaGetLastError();
 }
 
@@ -1727,10 +1750,10 @@ cudaError_t launch_force_tc(const sbx_ctx *ctx, const float *pairs, float *f4, d
   if (n_hang > 0) {
     cudaStream_t sg = both ? ctx->side : s;
     if (gtc) {
-      const int grid = std::min(ctx->n_gt_tiles, nsm);
+      const int grid = std::min(ctx->n_gt_tiles, std::max(1, ctx->hanging_ctas) * nsm);
       k_force_gen_tc<<<grid, GT_THREADS, ctx->gt_smem, sg>>>(
           ctx->d_gt_tiles, ctx->n_gt_tiles, ctx->d_gt_rec, ctx->d_gt_B, ctx->d_gt_boff, pairs, f4,
-          L, ctx->d_step, dt, ctx->d_flags);
+          L, ctx->d_step, dt, ctx->d_flags, ctx->gt_rec_off);
     } else {
       k_force_gen<<<ctx->n_gen_tiles, GEN_THREADS, ctx->gen_smem, sg>>>(
           ctx->d_gen_tiles, ctx->view(), ctx->d_gen_K, ctx->d_gen_koff, pairs, f4, L, ctx->d_step,
@@ -1742,7 +1765,8 @@ cudaError_t launch_force_tc(const sbx_ctx *ctx, const float *pairs, float *f4, d
   if (ctx->n_tc_tiles[0] > 0 && ctx->mixed_wht && ctx->wht_pat >= 0) {
     WhtF kw;
     for (int q = 0; q < 72; ++q) kw.blk[q] = (float)(ctx->wht.blk[q] * 0.125);
-    const int per_sm = ctx->walsh_ctas > 0 ? ctx->walsh_ctas : (gtc ? 4 : 6);
+    const int per_sm = ctx->walsh_ctas > 0 ? ctx->walsh_ctas
+                                           : (gtc ? (ctx->hanging_ctas > 1 ? 3 : 4) : 6);
     const int grid = std::max(1, std::min(ctx->wt_grid, per_sm * nsm));
     k_force_wht32<<<grid, WT_THREADS, ctx->wt_smem, s>>>(
         ctx->d_tc_tiles[0], ctx->n_tc_tiles[0], ctx->d_tc_rec, kw, pairs, f4, L, ctx->d_step, dt,

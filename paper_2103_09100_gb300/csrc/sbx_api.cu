@@ -1347,6 +1347,11 @@ int sbx_set_launch(sbx_ctx *ctx, int what, int value) {
       if (ctx->walsh_ctas != value) drop_graph(ctx);
       ctx->walsh_ctas = value;
       return SBX_OK;
+    case SBX_LAUNCH_HANGING_CTAS_PER_SM:
+      if (value < 1 || value > 2) return fail(ctx, SBX_EINVAL, "hanging-kernel CTAs per SM: 1 .. 2");
+      if (ctx->hanging_ctas != value) drop_graph(ctx);
+      ctx->hanging_ctas = value;
+      return SBX_OK;
     default:
       break;
   }
@@ -1386,6 +1391,9 @@ int sbx_get_launch(sbx_ctx *ctx, int what, int *value) {
       return SBX_OK;
     case SBX_LAUNCH_WALSH_CTAS_PER_SM:
       *value = ctx->walsh_ctas;
+      return SBX_OK;
+    case SBX_LAUNCH_HANGING_CTAS_PER_SM:
+      *value = ctx->hanging_ctas;
       return SBX_OK;
     default:
       break;
@@ -1511,7 +1519,8 @@ int sbx_set_step(sbx_ctx *ctx, int64_t n) {
 
 int read_field(sbx_ctx *ctx, int which, double *out, int64_t len) {
   if (!ctx) return SBX_EINVAL;
-  if (ctx->state_owner) return fail(ctx, SBX_ESTATE, "this context shares another context's state: only sbx_force applies");
+  if (ctx->state_owner && which != SBX_MASS)   // its own mass stays readable
+    return fail(ctx, SBX_ESTATE, "this context shares another context's state: only sbx_force applies");
   if (int rc = set_device(ctx)) return rc;
   ctx->err.clear();
   if (!ctx->have_mesh) return fail(ctx, SBX_ESTATE, "no mesh");

@@ -165,6 +165,8 @@ struct sbx_ctx {
   int64_t *d_gt_boff = nullptr;
   int n_gt_tiles = 0;
   size_t gt_smem = 0;
+  uint32_t gt_rec_off = 0;         // record offset in shared memory (after the largest B)
+  int hanging_ctas = 1;            // k_force_gen_tc CTAs per SM
   bool hanging_tc = true;          // k_force_gen_tc (default) instead of k_force_gen
   int walsh_ctas = 0;              // Walsh-kernel CTAs per SM (0: automatic)
   // the 8-node tiles by the Walsh-basis SIMT kernel instead of the tensor

@@ -147,6 +147,7 @@ def test_shared_state_rules():
     with pytest.raises(L.SbxError):
         L.sbx_share_state(C.ctx, A.ctx)
     L.sbx_share_state(B.ctx, A.ctx)
+    assert np.array_equal(B.field(L.SBX_MASS), A.field(L.SBX_MASS))   # its own mass
     for call in (lambda: B.step(1), lambda: B.field(), lambda: L.sbx_update(B.ctx, B.dt)):
         with pytest.raises(L.SbxError) as e:
             call()
