@@ -329,76 +329,6 @@ __device__ __forceinline__ void put_pair(float *p, double x0, double x1, double 
   st_hint(q + 2, make_float2(l1, l2), pol);
 }
 
-// Two adjacent nodes per thread (6 consecutive doubles of w, U_n and
-// U_{n-1}, 48 bytes: three 16-byte loads each; two float4 of f; 12 floats
-// of pairs), every load issued before any arithmetic (the update is bound
-// by memory latency x bytes in flight).  A trailing odd node is done by the
-// first thread.
-template <bool DAMPED>
-__global__ void __launch_bounds__(256) k_update_f32v(int64_t nn, const double *__restrict__ w,
-                                                     float4 *__restrict__ f,
-                                                     const double *__restrict__ uc,
-                                                     double *__restrict__ up,
-                                                     float *__restrict__ pairs, double a, double b,
-                                                     int zero_f, int32_t *flags, int64_t *d_step) {
-  bool bad = false;
-  const uint64_t stream = l2_evict_first(), keep = l2_evict_last();
-  const int64_t np = nn >> 1;
-  const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < np;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const double2 *w2 = reinterpret_cast<const double2 *>(w) + 3 * j;
-    const double2 *c2 = reinterpret_cast<const double2 *>(uc) + 3 * j;
-    double2 *p2 = reinterpret_cast<double2 *>(up) + 3 * j;
-    double2 wv[3], cv[3], pv[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      wv[q] = ld_nc_hint(w2 + q, stream);
-      cv[q] = ld_nc_hint(c2 + q, stream);
-      pv[q] = ld_hint(p2 + q, stream);
-    }
-    const float4 f0 = ld_hint(f + 2 * j, keep), f1 = ld_hint(f + 2 * j + 1, keep);
-    const double fv[6] = {f2d_bits(f0.x), f2d_bits(f0.y), f2d_bits(f0.z),
-                          f2d_bits(f1.x), f2d_bits(f1.y), f2d_bits(f1.z)};
-    double r[6];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      r[2 * q] = cdm_update<DAMPED>(wv[q].x, fv[2 * q], cv[q].x, pv[q].x, a, b);
-      r[2 * q + 1] = cdm_update<DAMPED>(wv[q].y, fv[2 * q + 1], cv[q].y, pv[q].y, a, b);
-    }
-#pragma unroll
-    for (int q = 0; q < 6; ++q) bad |= nonfinite(r[q]);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) st_hint(p2 + q, make_double2(r[2 * q], r[2 * q + 1]), stream);
-    float h[6], l[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) split_f64(r[q], h[q], l[q]);
-    float4 *pp = reinterpret_cast<float4 *>(pairs + 12 * j);   // (hx hy hz lx ly lz) x 2 nodes
-    st_hint(pp, make_float4(h[0], h[1], h[2], l[0]), keep);
-    st_hint(pp + 1, make_float4(l[1], l[2], h[3], h[4]), keep);
-    st_hint(pp + 2, make_float4(h[5], l[3], l[4], l[5]), keep);
-    if (zero_f) {
-      st_hint(f + 2 * j, zero4, keep);
-      st_hint(f + 2 * j + 1, zero4, keep);
-    }
-  }
-  if ((nn & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-    const int64_t i = nn - 1;
-    const float4 fv = f[i];
-    const double r0 = cdm_update<DAMPED>(w[3 * i], f2d_bits(fv.x), uc[3 * i], up[3 * i], a, b);
-    const double r1 = cdm_update<DAMPED>(w[3 * i + 1], f2d_bits(fv.y), uc[3 * i + 1], up[3 * i + 1], a, b);
-    const double r2 = cdm_update<DAMPED>(w[3 * i + 2], f2d_bits(fv.z), uc[3 * i + 2], up[3 * i + 2], a, b);
-    bad |= nonfinite(r0) || nonfinite(r1) || nonfinite(r2);
-    up[3 * i] = r0;
-    up[3 * i + 1] = r1;
-    up[3 * i + 2] = r2;
-    put_pair(pairs + 6 * i, r0, r1, r2);
-    if (zero_f) f[i] = zero4;
-  }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 1);
-  if (blockIdx.x == 0 && threadIdx.x == 0) *d_step += 1;
-}
-
 // UPD_U nodes per thread and round, all their loads issued before any
 // arithmetic (the update is bound by memory latency x parallelism).
 constexpr int UPD_U = 2;
@@ -536,15 +466,13 @@ cudaError_t launch_update_f32(const sbx_ctx *ctx, const double *uc, double *up, 
   const int64_t nn = ctx->N;
   const double cm = 1.0 - 0.5 * alpha * dt, cp = 1.0 + 0.5 * alpha * dt;
   float4 *f = reinterpret_cast<float4 *>(f4);
-  // one thread per pair of nodes; enough CTAs for every SM's resident share
-  const int64_t want = (nn / 2 + 255) / 256;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->n_sm * 8));
   if (alpha == 0.0)
-    k_update_f32v<false><<<grid, 256, 0, s>>>(nn, ctx->d_w, f, uc, up, pairs_out, 2.0, 1.0,
-                                              zero_f, ctx->d_flags, ctx->d_step);
+    k_update_f32<false><<<update_grid(ctx, 2 * nn), 256, 0, s>>>(
+        nn, ctx->d_w, f, uc, up, pairs_out, 2.0, 1.0, zero_f, ctx->d_flags, ctx->d_step);
   else
-    k_update_f32v<true><<<grid, 256, 0, s>>>(nn, ctx->d_w, f, uc, up, pairs_out, 2.0 / cp,
-                                             cm / cp, zero_f, ctx->d_flags, ctx->d_step);
+    k_update_f32<true><<<update_grid(ctx, 2 * nn), 256, 0, s>>>(
+        nn, ctx->d_w, f, uc, up, pairs_out, 2.0 / cp, cm / cp, zero_f, ctx->d_flags,
+        ctx->d_step);
   return cudaGetLastError();
 }
 

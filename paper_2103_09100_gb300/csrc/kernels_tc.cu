@@ -465,10 +465,8 @@ struct WhtF {
 };
 
 struct WtLayout {
-  uint32_t stage[2], u_off, d4, total;
+  uint32_t stage[2], u_off, total;
 };
-// two stages (record, node pairs), then the tile's nodes as FP32
-// differences to its first node, float4 (x, y, z, unused) per node
 __host__ __device__ inline WtLayout wt_layout(int rec_max, int nn_max) {
   WtLayout L;
   uint32_t o = 128;   // 2 record mbarriers
@@ -476,7 +474,6 @@ __host__ __device__ inline WtLayout wt_layout(int rec_max, int nn_max) {
   const uint32_t st = a128(L.u_off + 24u * (uint32_t)nn_max);
   L.stage[0] = o; o += st;
   L.stage[1] = o; o += st;
-  L.d4 = o; o += a128(16u * (uint32_t)nn_max);
   L.total = o;
   return L;
 }
@@ -501,7 +498,6 @@ __global__ void __launch_bounds__(WT_THREADS, 6)
   extern __shared__ __align__(128) unsigned char smem[];
   const WtLayout SL = wt_layout(rec_max, nn_max);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [0], [1] records of stage 0, 1
-  float4 *D4 = reinterpret_cast<float4 *>(smem + SL.d4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x;
   const uint32_t mb_rec0 = tc::smem_addr(&mbar[0]);
@@ -565,15 +561,6 @@ __global__ void __launch_bounds__(WT_THREADS, 6)
     const Stage S = stage_view(stage_base(s), SL.u_off);
     const int ncell = S.hdr[1], nn = S.hdr[2];
     const bool brick = S.hdr[3] == 1;
-    // every node of the tile once: FP32 difference to the tile's first node
-    // from the (hi, lo) pairs (a constant shift of all a cell's corners
-    // leaves its force unchanged: K_p annihilates translations)
-    for (int q = tid; q < nn; q += WT_THREADS) {
-      float d0, d1, d2;
-      node_diff(S.u + 6 * q, S.u, d0, d1, d2);
-      D4[q] = make_float4(d0, d1, d2, 0.0f);
-    }
-    __syncthreads();
     // o[r][k]: component r at corner k = a + 2 b + 4 c of this cell's force
     float o[3][8];
     if (fc < ncell) {
@@ -588,13 +575,9 @@ __global__ void __launch_bounds__(WT_THREADS, 6)
 #pragma unroll
         for (int k = 0; k < 8; ++k) lk[k] = (w4[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
       }
+      const float *ref = S.u + 6 * lk[0];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float4 v = D4[lk[k]];
-        o[0][k] = v.x;
-        o[1][k] = v.y;
-        o[2][k] = v.z;
-      }
+      for (int k = 0; k < 8; ++k) node_diff(S.u + 6 * lk[k], ref, o[0][k], o[1][k], o[2][k]);
       wht8f(o[0]);
       wht8f(o[1]);
       wht8f(o[2]);

@@ -61,3 +61,25 @@ def oracle_context(m, P, precision=L.SBX_PREC_FP64):
         L.sbx_destroy(ctx)
         raise
     return ctx
+
+
+class OracleMatrixSolver:
+    """A library context on the oracle's master matrices, stepped like a
+    Solver (initial / step / field / close)."""
+
+    def __init__(self, m, P, precision=L.SBX_PREC_FP64):
+        self.ctx = oracle_context(m, P, precision)
+        self.dt, self.n_dof = P.dt, m.n_dof
+
+    def initial(self, u0=None, v0=None):
+        L.set_initial(self.ctx, u0, v0, self.dt)
+
+    def step(self, n):
+        L.step_n(self.ctx, n, self.dt)
+
+    def field(self, which=L.SBX_U_N):
+        import numpy as np
+        return L.read_field(self.ctx, which, np.empty(self.n_dof))
+
+    def close(self):
+        L.sbx_destroy(self.ctx)
