@@ -326,8 +326,10 @@ def run_batched_only(args):
     stream = torch.cuda.Stream()
     S = Solver.from_mesh(mb, precision="fp32", n_rhs=B, stream=stream.cuda_stream)
     S.initial()
-    from paper_2103_09100_gb300 import autotune
-    tuned = autotune.tune(S, steps=5, repeats=3)
+    tuned = {"params": {}}
+    if not args.no_autotune:
+        from paper_2103_09100_gb300 import autotune
+        tuned = autotune.tune(S, steps=5, repeats=3)
     S.initial()
     S.step(args.warmup)
     L.sbx_prepare_steps(S.ctx, args.only_batched, S.dt, S.alpha)
@@ -357,10 +359,14 @@ def main():
     ap.add_argument("--hanging", default=None, choices=["simt", "tensor"],
                     help="mixed form: kernel for the hanging-node patterns (tensor: tcgen05, "
                          "TF32x3, the library's default; simt: FP32 FFMA)")
-    ap.add_argument("--walsh-ctas", type=int, default=0,
+    ap.add_argument("--walsh-ctas", type=int, default=None,
                     help="mixed form: Walsh-kernel CTAs per SM (0: the library's choice)")
     ap.add_argument("--hanging-ctas", type=int, default=None,
                     help="mixed form: CTAs per SM of the tensor-core hanging-pattern kernel")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch configuration for the headline "
+                         "(default: the autotuner picks it on this GPU, unless --hanging, "
+                         "--walsh-ctas or --hanging-ctas set it)")
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
@@ -399,10 +405,26 @@ def main():
     if args.precision == "mixed" and args.hanging is not None:
         L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_HANGING_KERNEL,
                          L.SBX_HANGING_TENSOR if args.hanging == "tensor" else L.SBX_HANGING_SIMT)
-    if args.precision == "mixed":
+    if args.precision == "mixed" and args.walsh_ctas is not None:
         L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_WALSH_CTAS_PER_SM, args.walsh_ctas)
-        if args.hanging_ctas is not None:
-            L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_HANGING_CTAS_PER_SM, args.hanging_ctas)
+    if args.precision == "mixed" and args.hanging_ctas is not None:
+        L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_HANGING_CTAS_PER_SM, args.hanging_ctas)
+    explicit = any(v is not None for v in (args.hanging, args.walsh_ctas, args.hanging_ctas))
+    launch = {"how": "library defaults"}
+    if args.precision == "mixed" and not explicit and not args.no_autotune:
+        from paper_2103_09100_gb300 import autotune
+        S.initial()
+        t = autotune.tune(S, steps=10, repeats=3, device_name=torch.cuda.get_device_name(local))
+        launch = {"how": "autotune.tune on this GPU (force-launch time, coordinate descent)",
+                  "params": {str(k): v for k, v in t["params"].items()},
+                  "force_ms_default": t["force_ms_default"], "force_ms_tuned": t["force_ms_tuned"]}
+    elif explicit:
+        launch = {"how": "set on the command line"}
+    if args.precision == "mixed":
+        launch["values"] = {nm: L.sbx_get_launch(S.ctx, w) for nm, w in (
+            ("hanging_kernel_tensor", L.SBX_LAUNCH_HANGING_KERNEL),
+            ("hanging_ctas_per_sm", L.SBX_LAUNCH_HANGING_CTAS_PER_SM),
+            ("walsh_ctas_per_sm", L.SBX_LAUNCH_WALSH_CTAS_PER_SM))}
     hanging_tc = (args.precision == "mixed" and
                   L.sbx_get_launch(S.ctx, L.SBX_LAUNCH_HANGING_KERNEL) == L.SBX_HANGING_TENSOR)
     S.initial()
@@ -496,7 +518,8 @@ def main():
                       "cells": mesh.n_cells, "dof": mesh.n_dof, "patterns": len(S.masters),
                       "precision": args.precision, "dt": S.dt,
                       "l2": "per-step working set %.0f MB > L2; no flush" % (bytes_step / 1e6),
-                      "parallelism": "replicas" if world > 1 else "1 GPU"},
+                      "parallelism": "replicas" if world > 1 else "1 GPU",
+                      "launch": launch},
            "roofline": roof, "gpu_launches": gpu_launches, "clocks": clocks, "e2e": e2e}
 
     forms = {}
@@ -565,7 +588,7 @@ def main():
                                          "force_ms_default": tuned["force_ms_default"],
                                          "force_ms_tuned": tuned["force_ms_tuned"]}}
         Bs.close()
-        # config 4: the layered-trench octree (~9.5M cells), mixed, 500 steps
+        # the layered-trench octree (7.7M cells, 42 patterns), mixed, 500 steps
         mt = og.config_layered_trench()
         free0, _ = torch.cuda.mem_get_info(local)
         T = Solver.from_mesh(mt, precision="mixed", device=local, stream=stream.cuda_stream)

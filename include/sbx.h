@@ -483,10 +483,12 @@ int sbx_classify_cells(sbx_ctx *ctx, int64_t n_cells, const int32_t *slot_node,
  * kernels (no counterpart in the paper: how Eq. Rintep's contraction is
  * mapped onto the GPU).  The results do not depend on it beyond rounding;
  * the step graphs are rebuilt after a change.
- *   SBX_LAUNCH_HANGING_KERNEL      mixed form: the patterns other than the
- *       identity-op 8-node cell on the tensor cores, TF32 x 3 with FP32
- *       accumulation in tensor memory (SBX_HANGING_TENSOR, the default),
- *       or on FP32 SIMT (SBX_HANGING_SIMT).
+ *   SBX_LAUNCH_HANGING_KERNEL      mixed and batched FP32 forms: the
+ *       patterns other than the identity-op 8-node cell on the tensor cores,
+ *       TF32 x 3 with FP32 accumulation in tensor memory
+ *       (SBX_HANGING_TENSOR; the mixed form's default), or on FP32 SIMT
+ *       (SBX_HANGING_SIMT; the batched form's default).  mesh_upload resets
+ *       it to the form's default.
  *   SBX_LAUNCH_WALSH_CTAS_PER_SM   mixed form: resident CTAs per SM of the
  *       Walsh-basis kernel, 1 .. 8, or 0 for the library's choice.
  *   SBX_LAUNCH_HANGING_CTAS_PER_SM mixed form: CTAs per SM of the

@@ -6,16 +6,20 @@ mesh's pattern mix and on the GPU.  ``tune`` measures it: for one solver
 it times the force launches (``sbx_profile``, CUDA events around every
 launch, summed over a few steps, median of repeats) for each value of each
 launch parameter in turn, keeps the fastest (coordinate descent in a fixed
-order) and leaves the solver configured with the result.  A result is a
+order) and leaves the solver configured with the result.  A candidate
+replaces the current value only when it is faster by more than
+``min_gain`` (a fraction; run-to-run spread of these timings is about 1 %),
+so that noise does not move the configuration away from the defaults.  A result is a
 plain table -- device name, mesh signature, parameter values and the
 measured times -- that ``save`` / ``load`` keep as JSON and ``apply`` sets
 on another solver of the same mesh.  The parameters change the rounding
 order of the reductions only, never the arithmetic.
 
 Searched parameters (``sbx_set_launch``):
-* batched form, per pattern class c (8-node, up to 16-node, larger cells):
-  most cells per tile and the shared-memory budget per CTA (which sets how
-  many CTAs share an SM);
+* batched form, per pattern class c (8-node, up to 16-node, larger
+  cells): most cells per tile and the shared-memory budget per CTA (which
+  sets how many CTAs share an SM); then the hanging-node classes on the
+  tensor cores or not (FP32 form);
 * mixed form: the kernel for the hanging-node patterns (tensor cores or
   FP32 SIMT), its CTAs per SM, and the Walsh kernel's CTAs per SM.
 """
@@ -39,9 +43,13 @@ def search_space(solver):
     """[(parameter, candidate values)] in the order they are tuned."""
     if solver.n_rhs > 1:
         space = []
+        # the hanging-node classes' SIMT tiles first, then whether the
+        # tensor cores beat them (FP32 form)
         for c in range(3):
             space.append((L.SBX_LAUNCH_BATCH_TILE_CELLS + c, BATCH_CELLS))
             space.append((L.SBX_LAUNCH_BATCH_SMEM_KB + c, BATCH_SMEM_KB))
+        if solver.precision == "fp32":
+            space.append((L.SBX_LAUNCH_HANGING_KERNEL, MIXED_HANGING))
         return space
     if solver.precision == "mixed":
         return [(L.SBX_LAUNCH_HANGING_KERNEL, MIXED_HANGING),
@@ -70,7 +78,7 @@ def force_ms(solver, steps, repeats):
     return float(np.median(t))
 
 
-def tune(solver, steps=10, repeats=3, device_name=None):
+def tune(solver, steps=10, repeats=3, device_name=None, min_gain=0.02):
     """Coordinate descent over ``search_space(solver)``; returns the table
     and leaves the solver configured with it."""
     space = search_space(solver)
@@ -91,13 +99,13 @@ def tune(solver, steps=10, repeats=3, device_name=None):
                 continue
             t = force_ms(solver, steps, repeats)
             trials.append((int(what), int(v), t))
-            if t < best_t:
+            if t < best_t * (1.0 - min_gain):
                 best_t, best_v = t, v
         L.sbx_set_launch(solver.ctx, what, best_v)
     params = {int(w): L.sbx_get_launch(solver.ctx, w) for w, _ in space}
     return {"device": device_name, "mesh": mesh_signature(solver), "params": params,
             "default_params": base, "force_ms_default": t_default, "force_ms_tuned": best_t,
-            "trials": trials, "steps": steps, "repeats": repeats}
+            "trials": trials, "steps": steps, "repeats": repeats, "min_gain": min_gain}
 
 
 def apply(solver, table):

@@ -9,7 +9,7 @@
 // 16-byte vector reduction.  No FP64 arithmetic runs per node or cell
 // (GB300's FP64 pipe is ~1/64 of FP32).
 //
-// Three kernels:
+// The kernels:
 //   k_force_wht32 (default for) the 8-node cell with the identity op (the
 //                bulk of a refined octree): the same tiles and pipeline as
 //                k_force_tc below, one thread per cell, and K_p applied in
@@ -30,11 +30,17 @@
 //                tcgen05.commit -> mbarrier);
 //                tcgen05.ld D (row = cell) times E_e h_e into shared memory;
 //                each node sums its incidences (per-tile list) in FP32.
-//   k_force_gen  every other pattern and op (hanging-node cells: a few per
-//                cent of the cells, scattered, up to 78 DOFs): 32 cells per
-//                CTA, FP32 K_p in shared memory, F = K_p d by FFMA, back to
-//                the cell frame (Sec. 3.2.2), one vector reduction per
-//                (cell, node).
+//   k_force_gen_tc  every other pattern and op (hanging-node cells: a few
+//                per cent of the cells, up to 78 DOFs) on the tensor cores
+//                (the default): tiles of up to 128 cells of one pattern,
+//                A = the cells' master-frame differences in tensor memory,
+//                B = K_p TF32 hi | lo bulk-copied per pattern, TF32 x 3.
+//   k_force_gen  the same cells on FP32 SIMT (SBX_HANGING_SIMT): 32 cells
+//                per CTA, FP32 K_p in shared memory, F = K_p d by FFMA,
+//                back to the cell frame (Sec. 3.2.2), one vector reduction
+//                per (cell, node).
+// and, for the batched FP32 form, k_force_batch_tc: the hanging-node
+// patterns' (cell, load case) rows on the tensor cores.
 //
 // B uses the canonical no-swizzle K-major layout: 8-row x 16-byte core
 // matrices, row groups nK * 128 B apart, K groups 128 B apart within a row

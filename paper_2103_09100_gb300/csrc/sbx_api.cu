@@ -608,6 +608,9 @@ int mesh_upload(sbx_ctx *ctx, int64_t n_nodes, int64_t n_cells, const int32_t *c
   ctx->prec = precision_mode;
   ctx->B = n_rhs;
   ctx->N = n_nodes;
+  // default kernel of the hanging-node patterns: tensor cores for one load
+  // case, FP32 SIMT for the batched form (measured faster there)
+  ctx->hanging_tc = n_rhs == 1;
   ctx->h_order = order;
   ctx->h_hs.resize(n_cells);
   for (int64_t s = 0; s < n_cells; ++s) ctx->h_hs[s] = hv[order[s]];

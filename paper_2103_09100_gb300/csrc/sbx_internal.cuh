@@ -167,7 +167,7 @@ struct sbx_ctx {
   size_t gt_smem = 0;
   uint32_t gt_rec_off = 0;         // record offset in shared memory (after the largest B)
   int hanging_ctas = 1;            // k_force_gen_tc CTAs per SM
-  bool hanging_tc = true;          // k_force_gen_tc (default) instead of k_force_gen
+  bool hanging_tc = true;          // the other patterns on the tensor cores (mesh_upload: B == 1)
   int walsh_ctas = 0;              // Walsh-kernel CTAs per SM (0: automatic)
   // the 8-node tiles by the Walsh-basis SIMT kernel instead of the tensor
   // cores (sbx_set_mixed_kernel)

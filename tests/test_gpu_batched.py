@@ -135,3 +135,26 @@ def test_batched_fp32_damped_and_force_readback():
         # the oracle returns R_ext - R_int of the last step, the library R_int - R_ext
         assert rel(-fg[:, b], f) < 1e-4
     S.close()
+
+
+def test_batched_fp32_other_tile_shapes():
+    # every class re-tiled (sbx_set_launch) on FP32 SIMT: only the
+    # reductions' order changes
+    m = _with_sources(og.config_corner_cube(), 32, 11, t1_scale=10.0)
+    P0 = cdm.make_problem(m, rhs=0)
+    S = Solver.from_mesh(m, precision="fp32", n_rhs=32, dt=P0.dt)
+    L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_HANGING_KERNEL, L.SBX_HANGING_SIMT)
+    for c, (cells, kb) in enumerate([(64, 150), (8, 56), (16, 72)]):
+        L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_BATCH_TILE_CELLS + c, cells)
+        L.sbx_set_launch(S.ctx, L.SBX_LAUNCH_BATCH_SMEM_KB + c, kb)
+        assert L.sbx_get_launch(S.ctx, L.SBX_LAUNCH_BATCH_TILE_CELLS + c) == cells
+        assert L.sbx_get_launch(S.ctx, L.SBX_LAUNCH_BATCH_SMEM_KB + c) == kb
+    S.initial()
+    S.step(500)
+    g = S.field(L.SBX_U_N).reshape(-1, 32)
+    for b in (0, 9, 31):
+        P = cdm.make_problem(m, dt=P0.dt, rhs=b)
+        u, up = cdm.initial_state(P)
+        u, _, _, _ = cdm.run(P, 500, u, up, threads=4)
+        assert rel(g[:, b], u) < 1e-5
+    S.close()
