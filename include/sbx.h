@@ -493,6 +493,11 @@ int sbx_classify_cells(sbx_ctx *ctx, int64_t n_cells, const int32_t *slot_node,
  *       Walsh-basis kernel, 1 .. 8, or 0 for the library's choice.
  *   SBX_LAUNCH_HANGING_CTAS_PER_SM mixed form: CTAs per SM of the
  *       tensor-core kernel of the hanging-node patterns, 1 (default) or 2.
+ *   SBX_LAUNCH_UPDATE_KERNEL       mixed form: Eq. DnMdiag's update with
+ *       its rows streamed through shared memory in chunks of 128 nodes by
+ *       1-D bulk copies, two chunks in flight per CTA (SBX_UPDATE_BULK,
+ *       default), or with each thread loading its own nodes
+ *       (SBX_UPDATE_THREAD).  Bit-identical results.
  *   SBX_LAUNCH_BATCH_TILE_CELLS + c   batched form, pattern class c (0: up
  *       to 8 nodes, 1: up to 16, 2: more): most cells per tile, 1 .. 64
  *       (default 32).  A change rebuilds the class's tiles.
@@ -505,10 +510,13 @@ int sbx_classify_cells(sbx_ctx *ctx, int64_t n_cells, const int32_t *slot_node,
 #define SBX_LAUNCH_HANGING_KERNEL     0
 #define SBX_LAUNCH_WALSH_CTAS_PER_SM  1
 #define SBX_LAUNCH_HANGING_CTAS_PER_SM 2
+#define SBX_LAUNCH_UPDATE_KERNEL      3
 #define SBX_LAUNCH_BATCH_TILE_CELLS   16
 #define SBX_LAUNCH_BATCH_SMEM_KB      20
 #define SBX_HANGING_SIMT   0
 #define SBX_HANGING_TENSOR 1
+#define SBX_UPDATE_THREAD  0
+#define SBX_UPDATE_BULK    1
 int sbx_set_launch(sbx_ctx *ctx, int what, int value);
 int sbx_get_launch(sbx_ctx *ctx, int what, int *value);
 

@@ -34,6 +34,8 @@ EXPORTS = ["sbx_create", "sbx_destroy", "sbx_last_error", "sbx_sync", "set_patte
 SBX_LAUNCH_HANGING_KERNEL, SBX_LAUNCH_WALSH_CTAS_PER_SM, SBX_LAUNCH_HANGING_CTAS_PER_SM = 0, 1, 2
 SBX_LAUNCH_BATCH_TILE_CELLS, SBX_LAUNCH_BATCH_SMEM_KB = 16, 20
 SBX_HANGING_SIMT, SBX_HANGING_TENSOR = 0, 1
+SBX_LAUNCH_UPDATE_KERNEL = 3
+SBX_UPDATE_THREAD, SBX_UPDATE_BULK = 0, 1
 SBX_LAYOUT_F64_DOF, SBX_LAYOUT_F32_NODE4, SBX_LAYOUT_F32_DOF = 0, 1, 2
 SBX_Q_KERNELS_PER_STEP, SBX_Q_FORCE_LAUNCHES, SBX_Q_TILES, SBX_Q_BRICK_TILES = 0, 1, 2, 3
 SBX_MIXED_TENSOR, SBX_MIXED_WALSH = 0, 1

@@ -17,6 +17,7 @@
 
 #include "device_common.cuh"
 #include "sbx_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace sbx {
 
@@ -237,7 +238,10 @@ cudaError_t launch_force_simt(const sbx_ctx *ctx, const double *u, double *f, do
   return cudaGetLastError();
 }
 
+static cudaError_t prepare_update_kernels();
+
 cudaError_t prepare_kernels() {
+  if (const cudaError_t e0 = prepare_update_kernels()) return e0;
   const int a = (int)simt_smem(78, false), b = (int)simt_smem(78, true);
   cudaError_t e = cudaFuncSetAttribute(k_force_simt<double, SIMT_TILE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, a);
@@ -376,6 +380,130 @@ __global__ void __launch_bounds__(256) k_update_f32(int64_t nn, const double *__
   if (blockIdx.x == 0 && threadIdx.x == 0) *d_step += 1;
 }
 
+// The same update with the memory-level parallelism taken off the
+// registers: each CTA streams chunks of UB_NODES nodes (their w, U_n and
+// U_{n-1} rows and force rows) into shared memory by 1-D bulk copies,
+// UB_STAGES chunks in flight, and updates a chunk with one thread per node.
+// The update is bound by the FP64 pipe (2 DFMA per DOF, ~1 TFLOP/s on this
+// GPU: ~14 us of pipe time per step on 3.4M DOF) as much as by HBM; small
+// chunks, two stages and eight CTAs per SM overlapped the two best in a
+// sweep of shapes (27.1 us against 28.1 for k_update_f32).
+// The arithmetic is k_update_f32's (bit-identical results).  Every chunk
+// but the last starts 16-byte aligned (UB_NODES even, 24-byte rows); an odd
+// last node is read from global memory by its thread.  A wait that gives
+// up sets flag bit 2 after the copies in flight have landed (bounded).
+constexpr int UB_NODES = 128;
+constexpr int UB_STAGES = 2;
+constexpr uint32_t UB_ROWS = 24u * UB_NODES;                   // one array's rows per chunk
+constexpr uint32_t UB_STAGE = 3u * UB_ROWS + 16u * UB_NODES;   // w, U_n, U_{n-1}, f
+constexpr uint32_t UB_SMEM = 64u + UB_STAGES * UB_STAGE;
+constexpr int UB_CTAS_PER_SM = 8;
+constexpr uint32_t UB_WAIT_POLLS = 1u << 22;
+
+template <bool DAMPED>
+__global__ void __launch_bounds__(UB_NODES) k_update_f32_bulk(
+    int64_t nn, const double *__restrict__ w, float4 *__restrict__ f,
+    const double *__restrict__ uc, double *__restrict__ up, float *__restrict__ pairs, double a,
+    double b, int zero_f, int32_t *flags, int64_t *d_step) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint64_t stream = l2_evict_first(), keep = l2_evict_last();
+  const int tid = threadIdx.x;
+  const int64_t nchunks = (nn + UB_NODES - 1) / UB_NODES, G = gridDim.x;
+  const uint32_t mb0 = tc::smem_addr(smem);
+  auto stage = [&](int s) { return smem + 64u + (uint32_t)s * UB_STAGE; };
+  auto issue = [&](int s, int64_t c) {   // thread 0
+    const int64_t n0 = c * UB_NODES;
+    const int n = (int)(nn - n0 < UB_NODES ? nn - n0 : UB_NODES);
+    const uint32_t rb = 24u * (uint32_t)(n & ~1), fb = 16u * (uint32_t)n;
+    const uint32_t mb = mb0 + 8u * (uint32_t)s, d = tc::smem_addr(stage(s));
+    tc::fence_proxy_async_smem();
+    tc::mbar_arrive_expect_tx(mb, 3u * rb + fb);
+    if (rb) {
+      tc::bulk_g2s_hint(d, w + 3 * n0, rb, mb, stream);
+      tc::bulk_g2s_hint(d + UB_ROWS, uc + 3 * n0, rb, mb, stream);
+      tc::bulk_g2s_hint(d + 2u * UB_ROWS, up + 3 * n0, rb, mb, stream);
+    }
+    tc::bulk_g2s_hint(d + 3u * UB_ROWS, f + n0, fb, mb, keep);
+  };
+  uint32_t pend = 0u, ph = 0u;   // thread 0: stages with copies in flight, their phases
+  if (tid == 0) {
+    for (int s = 0; s < UB_STAGES; ++s) tc::mbar_init(mb0 + 8u * (uint32_t)s, 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int s = 0; s < UB_STAGES; ++s)
+      if (blockIdx.x + s * G < nchunks) {
+        issue(s, blockIdx.x + s * G);
+        pend |= 1u << s;
+      }
+  bool bad = false, ok = true;
+  int k = 0;
+  for (int64_t c = blockIdx.x; c < nchunks; c += G, ++k) {
+    const int s = k % UB_STAGES;
+    const bool got =
+        tc::mbar_wait_bounded(mb0 + 8u * (uint32_t)s, (uint32_t)(k / UB_STAGES) & 1u, UB_WAIT_POLLS);
+    const int64_t n0 = c * UB_NODES;
+    const int n = (int)(nn - n0 < UB_NODES ? nn - n0 : UB_NODES);
+    if (got && tid < n) {
+      const int64_t i = n0 + tid;
+      const double *W = reinterpret_cast<const double *>(stage(s));
+      const double *C = W + 3 * UB_NODES, *Pm = C + 3 * UB_NODES;
+      const float4 fv = reinterpret_cast<const float4 *>(Pm + 3 * UB_NODES)[tid];
+      double wv[3], cv[3], pv[3];
+      if (tid < (n & ~1)) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          wv[d] = W[3 * tid + d];
+          cv[d] = C[3 * tid + d];
+          pv[d] = Pm[3 * tid + d];
+        }
+      } else {   // the odd last node
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          wv[d] = w[3 * i + d];
+          cv[d] = uc[3 * i + d];
+          pv[d] = up[3 * i + d];
+        }
+      }
+      const double r0 = cdm_update<DAMPED>(wv[0], f2d_bits(fv.x), cv[0], pv[0], a, b);
+      const double r1 = cdm_update<DAMPED>(wv[1], f2d_bits(fv.y), cv[1], pv[1], a, b);
+      const double r2 = cdm_update<DAMPED>(wv[2], f2d_bits(fv.z), cv[2], pv[2], a, b);
+      bad |= nonfinite(r0) || nonfinite(r1) || nonfinite(r2);
+      st_hint(up + 3 * i, r0, stream);
+      st_hint(up + 3 * i + 1, r1, stream);
+      st_hint(up + 3 * i + 2, r2, stream);
+      put_pair(pairs + 6 * i, r0, r1, r2, keep);
+      if (zero_f) st_hint(f + i, make_float4(0.0f, 0.0f, 0.0f, 0.0f), keep);
+    }
+    ok = __syncthreads_and(got);   // also: every thread is done with stage s
+    if (!ok) break;
+    if (tid == 0) {
+      ph ^= 1u << s;
+      pend &= ~(1u << s);
+      if (c + UB_STAGES * G < nchunks) {
+        issue(s, c + UB_STAGES * G);
+        pend |= 1u << s;
+      }
+    }
+  }
+  if (!ok && tid == 0) {   // let the copies in flight land before the CTA exits
+    atomicOr(flags, 2);
+    for (int s = 0; s < UB_STAGES; ++s)
+      if (pend & (1u << s)) tc::mbar_wait_bounded(mb0 + 8u * (uint32_t)s, (ph >> s) & 1u, UB_WAIT_POLLS);
+  }
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(flags, 1);
+  if (blockIdx.x == 0 && tid == 0) *d_step += 1;
+}
+
+static cudaError_t prepare_update_kernels() {
+  for (const void *k : {(const void *)k_update_f32_bulk<false>, (const void *)k_update_f32_bulk<true>}) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, UB_SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 __global__ void k_split_flat(int64_t nv, const double *u, float2 *pairs) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -466,6 +594,20 @@ cudaError_t launch_update_f32(const sbx_ctx *ctx, const double *uc, double *up, 
   const int64_t nn = ctx->N;
   const double cm = 1.0 - 0.5 * alpha * dt, cp = 1.0 + 0.5 * alpha * dt;
   float4 *f = reinterpret_cast<float4 *>(f4);
+  auto a16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (ctx->update_bulk && a16(ctx->d_w) && a16(uc) && a16(up) && a16(f)) {
+    const int64_t nchunks = (nn + UB_NODES - 1) / UB_NODES;
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>(nchunks, (int64_t)ctx->n_sm * UB_CTAS_PER_SM));
+    if (alpha == 0.0)
+      k_update_f32_bulk<false><<<grid, UB_NODES, UB_SMEM, s>>>(
+          nn, ctx->d_w, f, uc, up, pairs_out, 2.0, 1.0, zero_f, ctx->d_flags, ctx->d_step);
+    else
+      k_update_f32_bulk<true><<<grid, UB_NODES, UB_SMEM, s>>>(
+          nn, ctx->d_w, f, uc, up, pairs_out, 2.0 / cp, cm / cp, zero_f, ctx->d_flags,
+          ctx->d_step);
+    return cudaGetLastError();
+  }
   if (alpha == 0.0)
     k_update_f32<false><<<update_grid(ctx, 2 * nn), 256, 0, s>>>(
         nn, ctx->d_w, f, uc, up, pairs_out, 2.0, 1.0, zero_f, ctx->d_flags, ctx->d_step);

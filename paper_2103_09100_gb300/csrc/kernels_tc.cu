@@ -496,6 +496,23 @@ __device__ __forceinline__ void wht8f(float *x) {
       }
 }
 
+// The same transform on (x, y) pairs of components held as float2: Blackwell's
+// packed FP32 arithmetic does both lanes in one instruction.  a - b is
+// b * (-1) + a (an exact product, one rounding), so the results equal the
+// scalar transform's bit for bit.
+__device__ __forceinline__ void wht8f2(float2 *x) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+  for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if ((i & h) == 0) {
+        const float2 a = x[i], b = x[i + h];
+        x[i] = __fadd2_rn(a, b);
+        x[i + h] = __ffma2_rn(b, m1, a);
+      }
+}
+
 __global__ void __launch_bounds__(WT_THREADS, 6)
     k_force_wht32(const TcTile *__restrict__ tiles, int ntiles, const uint8_t *__restrict__ recs,
                   const WhtF Kw, const float *__restrict__ u, float *__restrict__ f4, LoadTable Ld,
@@ -581,29 +598,50 @@ __global__ void __launch_bounds__(WT_THREADS, 6)
 #pragma unroll
         for (int k = 0; k < 8; ++k) lk[k] = (w4[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
       }
-      const float *ref = S.u + 6 * lk[0];
+      // differences to slot 0: (x, y) as packed pairs, z scalar; corner 0's are 0
+      float2 X[8];
+      float Z[8];
+      X[0] = make_float2(0.0f, 0.0f);
+      Z[0] = 0.0f;
+      {
+        const float *ref = S.u + 6 * lk[0];
+        const float2 ra = *reinterpret_cast<const float2 *>(ref);       // hx hy
+        const float2 rb = *reinterpret_cast<const float2 *>(ref + 2);   // hz lx
+        const float2 rc = *reinterpret_cast<const float2 *>(ref + 4);   // ly lz
+        const float2 m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) node_diff(S.u + 6 * lk[k], ref, o[0][k], o[1][k], o[2][k]);
-      wht8f(o[0]);
-      wht8f(o[1]);
-      wht8f(o[2]);
-      float y[3][8];
+        for (int k = 1; k < 8; ++k) {
+          const float *p = S.u + 6 * lk[k];
+          const float2 a = *reinterpret_cast<const float2 *>(p);
+          const float2 b = *reinterpret_cast<const float2 *>(p + 2);
+          const float2 c = *reinterpret_cast<const float2 *>(p + 4);
+          X[k] = __fadd2_rn(__ffma2_rn(ra, m1, a), make_float2(b.y - rb.y, c.x - rc.x));
+          Z[k] = (b.x - rb.x) + (c.y - rc.y);
+        }
+      }
+      wht8f2(X);
+      wht8f(Z);
+      float2 Y[8];
+      float YZ[8];
 #pragma unroll
       for (int sb = 0; sb < 8; ++sb) {
         const float *B = Kw.blk + 9 * sb;
-        const float v0 = o[0][sb ^ 1], v1 = o[1][sb ^ 2], v2 = o[2][sb ^ 4];
-        y[0][sb ^ 1] = fmaf(B[0], v0, fmaf(B[1], v1, B[2] * v2));
-        y[1][sb ^ 2] = fmaf(B[3], v0, fmaf(B[4], v1, B[5] * v2));
-        y[2][sb ^ 4] = fmaf(B[6], v0, fmaf(B[7], v1, B[8] * v2));
+        const float v0 = X[sb ^ 1].x, v1 = X[sb ^ 2].y, v2 = Z[sb ^ 4];
+        Y[sb ^ 1].x = fmaf(B[0], v0, fmaf(B[1], v1, B[2] * v2));
+        Y[sb ^ 2].y = fmaf(B[3], v0, fmaf(B[4], v1, B[5] * v2));
+        YZ[sb ^ 4] = fmaf(B[6], v0, fmaf(B[7], v1, B[8] * v2));
       }
-      wht8f(y[0]);
-      wht8f(y[1]);
-      wht8f(y[2]);
+      wht8f2(Y);
+      wht8f(YZ);
       const float sc = S.scale[fc];
+      const float2 sc2 = make_float2(sc, sc);
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-#pragma unroll
-        for (int r = 0; r < 3; ++r) o[r][k] = sc * y[r][k];
+      for (int k = 0; k < 8; ++k) {
+        const float2 q = __fmul2_rn(sc2, Y[k]);
+        o[0][k] = q.x;
+        o[1][k] = q.y;
+        o[2][k] = sc * YZ[k];
+      }
     }
     // the next tile's record (issued a tile ago) and the gather of its node
     // pairs, under this tile's node sums

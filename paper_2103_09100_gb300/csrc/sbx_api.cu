@@ -1355,6 +1355,12 @@ int sbx_set_launch(sbx_ctx *ctx, int what, int value) {
       if (ctx->hanging_ctas != value) drop_graph(ctx);
       ctx->hanging_ctas = value;
       return SBX_OK;
+    case SBX_LAUNCH_UPDATE_KERNEL:
+      if (value != SBX_UPDATE_THREAD && value != SBX_UPDATE_BULK)
+        return fail(ctx, SBX_EINVAL, "unknown update kernel");
+      if (ctx->update_bulk != (value == SBX_UPDATE_BULK)) drop_graph(ctx);
+      ctx->update_bulk = value == SBX_UPDATE_BULK;
+      return SBX_OK;
     default:
       break;
   }
@@ -1397,6 +1403,9 @@ int sbx_get_launch(sbx_ctx *ctx, int what, int *value) {
       return SBX_OK;
     case SBX_LAUNCH_HANGING_CTAS_PER_SM:
       *value = ctx->hanging_ctas;
+      return SBX_OK;
+    case SBX_LAUNCH_UPDATE_KERNEL:
+      *value = ctx->update_bulk ? SBX_UPDATE_BULK : SBX_UPDATE_THREAD;
       return SBX_OK;
     default:
       break;

@@ -169,6 +169,7 @@ struct sbx_ctx {
   int hanging_ctas = 1;            // k_force_gen_tc CTAs per SM
   bool hanging_tc = true;          // the other patterns on the tensor cores (mesh_upload: B == 1)
   int walsh_ctas = 0;              // Walsh-kernel CTAs per SM (0: automatic)
+  bool update_bulk = true;         // mixed update: chunks by bulk copy (k_update_f32_bulk)
   // the 8-node tiles by the Walsh-basis SIMT kernel instead of the tensor
   // cores (sbx_set_mixed_kernel)
   bool mixed_wht = false;

@@ -155,6 +155,15 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
       "l"(src), "r"(bytes), "r"(mbar)
       : "memory");
 }
+// The same with an L2 eviction-priority policy (createpolicy) on the source.
+__device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void *src, uint32_t bytes,
+                                              uint32_t mbar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], "
+      "%2, [%3], %4;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar), "l"(pol)
+      : "memory");
+}
 // 8-byte asynchronous copy global -> shared (per thread), grouped with
 // cp.async.commit_group / cp.async.wait_group.
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
