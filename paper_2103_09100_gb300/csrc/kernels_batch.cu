@@ -15,7 +15,9 @@
 //   3. E_e h_e Q^T acc goes straight to f with one atomic reduction per
 //      (cell, node DOF), coalesced over the warp's 32 cases (T = float: f is
 //      FP32; T = double: FP64).
-// T = float: FP32 contraction; T = double: FP64.  The update is FP64.
+// T = float: FP32 contraction, on Blackwell's packed FP32 pairs (two rows of
+// K_p per instruction; the regular cell's Walsh transforms on its (x, y)
+// components); T = double: FP64.  The update is FP64.
 #include <math.h>
 #include <string.h>
 
@@ -93,12 +95,138 @@ __device__ __forceinline__ void wht8_t(T *x) {
       }
 }
 
+// The same transform on pairs of values held as float2 (Blackwell's packed
+// FP32 arithmetic: both lanes in one instruction; a - b as b * (-1) + a, an
+// exact product and one rounding, so bit-identical to the scalar form).
+__device__ __forceinline__ void wht8_f2(float2 *x) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+  for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if ((i & h) == 0) {
+        const float2 a = x[i], b = x[i + h];
+        x[i] = __fadd2_rn(a, b);
+        x[i + h] = __ffma2_rn(b, m1, a);
+      }
+}
+
 // The regular 8-node cell's K_p as eight 3 x 3 blocks in the Walsh basis
 // of its corners (already divided by 8), in the kernel's number type.
 template <typename T>
 struct WhtB {
   T blk[72];
 };
+
+// The FP32 form of one CTA's cells (steps 2 and 3 above), with the
+// arithmetic on packed FP32 pairs: the differences as (hi - hi_0, lo - lo_0)
+// pairs; the dense contraction two rows of K_p at a time (acc[i], acc[i + 1]
+// += (K_p[j][i], K_p[j][i + 1]) d_j, the fused multiply-add of the scalar
+// form per lane); the regular cell's transforms on its (x, y) components.
+// Results equal the scalar FP32 arithmetic bit for bit.
+template <int MM>
+__device__ __forceinline__ void force_cells_f32(const unsigned char *smem, const BSmem &SL,
+                                                int ncell, int n, int m, int pat,
+                                                const uint8_t *sym, const double *scale,
+                                                const int32_t *nodes, const uint16_t *lid,
+                                                float *__restrict__ f, int B, int b0, int warp,
+                                                int lane, int wht_pat, const WhtB<float> &Kw) {
+  const float *Ks = reinterpret_cast<const float *>(smem + SL.K);
+  const float2 *uu = reinterpret_cast<const float2 *>(smem + SL.u);
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  for (int c = warp; c < ncell; c += BT_WARPS) {
+    const int op = sym[c];
+    const int p0 = op_perm_of(op, 0), p1 = op_perm_of(op, 1), p2 = op_perm_of(op, 2);
+    const int q0 = lid[c];
+    const float s = (float)scale[c];
+    // (hi - hi_0) + (lo - lo_0) of node q, direction a, this lane's case
+    auto dif = [&](int q, int a) {
+      const float2 t = __ffma2_rn(uu[(q0 * 3 + a) * BC + lane], m1, uu[(q * 3 + a) * BC + lane]);
+      return t.x + t.y;
+    };
+    // E h Q^T of entry i (node slot i / 3) into f, one reduction per entry
+    auto emit = [&](int i, float val) {
+      const int k = i / 3, r = i % 3;
+      const int a = r == 0 ? p0 : (r == 1 ? p1 : p2);
+      const float v = ((op >> r) & 1) ? -s * val : s * val;
+      atomicAdd(&f[(3 * (int64_t)nodes[lid[k * ncell + c]] + a) * B + b0 + lane], v);
+    };
+    float2 acc[MM / 2];   // every entry below m is set on either path
+    auto put = [&](int i, float v) {
+      if (i & 1) acc[i / 2].y = v;
+      else acc[i / 2].x = v;
+    };
+    if (MM == 24 && op == 0 && pat == wht_pat) {
+      // regular cell: f = T^T blockdiag(Kh) T d / 8 with the Walsh transform
+      // T over the corners; (x, y) components packed, z scalar
+      float2 X[8];
+      float Z[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int q = lid[k * ncell + c];
+        X[k] = make_float2(dif(q, 0), dif(q, 1));
+        Z[k] = dif(q, 2);
+      }
+      wht8_f2(X);
+      wht8_t(Z);
+      float2 Y[8];
+      float YZ[8];
+#pragma unroll
+      for (int sb = 0; sb < 8; ++sb) {
+        const float *Bk = Kw.blk + 9 * sb;
+        const float v0 = X[sb ^ 1].x, v1 = X[sb ^ 2].y, v2 = Z[sb ^ 4];
+        Y[sb ^ 1].x = Bk[0] * v0 + Bk[1] * v1 + Bk[2] * v2;
+        Y[sb ^ 2].y = Bk[3] * v0 + Bk[4] * v1 + Bk[5] * v2;
+        YZ[sb ^ 4] = Bk[6] * v0 + Bk[7] * v1 + Bk[8] * v2;
+      }
+      wht8_f2(Y);
+      wht8_t(YZ);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        put(3 * k, Y[k].x);
+        put(3 * k + 1, Y[k].y);
+        put(3 * k + 2, YZ[k]);
+      }
+    } else {
+#pragma unroll
+    for (int i = 0; i < MM / 2; ++i) acc[i] = make_float2(0.0f, 0.0f);
+    // acc += K_p row j (two entries per instruction) times d_j
+    auto row = [&](int j, float dj) {
+      const float *kr = Ks + j * MM;
+      const float2 dd = make_float2(dj, dj);
+#pragma unroll
+      for (int i = 0; i < MM; i += 4) {
+        const float4 kv = *reinterpret_cast<const float4 *>(kr + i);
+        acc[i / 2] = __ffma2_rn(make_float2(kv.x, kv.y), dd, acc[i / 2]);
+        acc[i / 2 + 1] = __ffma2_rn(make_float2(kv.z, kv.w), dd, acc[i / 2 + 1]);
+      }
+    };
+    if constexpr (MM <= 24) {
+#pragma unroll
+      for (int k = 0; k < MM / 3; ++k)
+        if (k < n) {
+          const int q = lid[k * ncell + c];
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const int a = r == 0 ? p0 : (r == 1 ? p1 : p2);
+            const float x = dif(q, a);
+            row(3 * k + r, ((op >> r) & 1) ? -x : x);
+          }
+        }
+    } else {
+      for (int j = 0; j < m; ++j) {
+        const int k = j / 3, r = j - 3 * (j / 3);
+        const int a = r == 0 ? p0 : (r == 1 ? p1 : p2);
+        const float x = dif(lid[k * ncell + c], a);
+        row(j, ((op >> r) & 1) ? -x : x);
+      }
+    }
+    }
+#pragma unroll
+    for (int i = 0; i < MM; ++i)
+      if (i < m) emit(i, (i & 1) ? acc[i / 2].y : acc[i / 2].x);
+  }
+}
 
 template <typename T, int MM>
 __global__ void __launch_bounds__(BT_THREADS, 2)
@@ -148,6 +276,10 @@ __global__ void __launch_bounds__(BT_THREADS, 2)
   }
   __syncthreads();
 
+  if constexpr (sizeof(T) == 4) {
+    force_cells_f32<MM>(smem, SL, ncell, n, m, pat, sym, scale, nodes, lid,
+                        reinterpret_cast<float *>(fv), B, b0, warp, lane, wht_pat, Kw);
+  } else
   for (int c = warp; c < ncell; c += BT_WARPS) {
     const int op = sym[c];
     const int p0 = op_perm_of(op, 0), p1 = op_perm_of(op, 1), p2 = op_perm_of(op, 2);
