@@ -344,6 +344,92 @@ def run_batched_only(args):
     S.close()
 
 
+def run_nodecut(args):
+    """The node-cut path (Sec. 4's partitioned explicit solver) on one GPU:
+    the parts of a Morton-range partition of the cavity mesh, each with its
+    own contexts, held by one process and stepped in turn: interface cells'
+    force, pack, exchange of each cut-node block with each neighbour (device
+    copies), interior cells' force, the canonical interface sum, update.
+    Reports the step time, the split into own work (t_C) and exchange plus
+    sum (t_W) that Sec. 4's timing study uses, and the difference from the
+    single-domain solver after the same steps."""
+    import torch
+    import octree_gen as og
+    from paper_2103_09100_gb300 import Solver, _lib as L, build, nodecut
+    from paper_2103_09100_gb300.partition import partition
+    build.build()
+    m = og.config_cavity_cube()
+    P = args.nodecut
+    steps = args.steps if args.steps != 20000 else 200
+    parts = partition(m.slot_node, P, fixed_nodes=m.fixed_nodes, sources=m.sources,
+                      weight=((m.slot_node >= 0).sum(1) ** 2))
+    eng = [nodecut.NodeCutSolver(p, m.mask, m.h, m.E, m.rho, m.nu, precision="mixed",
+                                 overlap=True) for p in parts]
+    dt = nodecut.setup_together(eng, 0.5)
+    nodecut.step_neighbours_together(eng, args.warmup)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    nodecut.step_neighbours_together(eng, steps)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t
+    # the split of a step, phases synchronised (gives up their overlap)
+    tc = tw = 0.0
+    n_split = 20
+    for _ in range(n_split):
+        t0 = time.perf_counter()
+        if not all([e.force_interface() for e in eng]):
+            raise RuntimeError("node-cut parts out of step")
+        for e in eng:
+            e.pack()
+        for e in eng:
+            e.stream.synchronize()
+        t1 = time.perf_counter()
+        nodecut.exchange_together(eng)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        for e in eng:
+            e.force_interior()
+        for e in eng:
+            e.stream.synchronize()
+        t3 = time.perf_counter()
+        for e in eng:
+            e.sum(e.recv)
+        for e in eng:
+            e.stream.synchronize()
+        t4 = time.perf_counter()
+        for e in eng:
+            e.update()
+        for e in eng:
+            e.stream.synchronize()
+        t5 = time.perf_counter()
+        tc += (t1 - t0) + (t3 - t2) + (t5 - t4)
+        tw += (t2 - t1) + (t4 - t3)
+    n_total = args.warmup + steps + n_split
+    ug = np.zeros((m.n_nodes, 3))
+    for e in eng:
+        ug[e.part.nodes] = e.field(L.SBX_U_N).reshape(-1, 3)
+    S = Solver.from_mesh(m, precision="mixed", dt=dt)
+    S.initial()
+    S.step(n_total)
+    ref = S.field(L.SBX_U_N).reshape(-1, 3)
+    S.close()
+    err = float(np.linalg.norm(ug - ref) / max(np.linalg.norm(ref), 1e-300))
+    out = {"form": "nodecut", "parts": P, "value": m.n_dof * steps / el, "unit": UNIT,
+           "ms_per_step": 1e3 * el / steps, "steps": steps,
+           "t_C_ms": 1e3 * tc / n_split, "t_W_ms": 1e3 * tw / n_split,
+           "neighbours": [len(e.plan.neighbours) for e in eng],
+           "cut_nodes": [int(len(e.part.cut_local)) for e in eng],
+           "interface_cells": [e.n_interface_cells for e in eng],
+           "rel_err_vs_single_domain": err, "err_steps": n_total,
+           "workload": "%s (%d cells, %d DOF), %d parts on one GPU" % (m.name, m.n_cells,
+                                                                      m.n_dof, P),
+           "timing": "host clock around the Python-driven steps (no step graphs; the parts "
+                     "take turns on the GPU)"}
+    for e in eng:
+        e.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,6 +460,10 @@ def main():
     ap.add_argument("--only-batched", type=int, default=0, metavar="STEPS",
                     help="diagnostics: time only the batched form for STEPS steps "
                          "(its own JSON line; for profiling)")
+    ap.add_argument("--nodecut", type=int, default=0, metavar="PARTS",
+                    help="the node-cut path on this GPU: the cavity mesh cut into PARTS parts "
+                         "held by one process, neighbour exchange with overlap (its own JSON "
+                         "line; --steps timed steps, default 200)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -383,6 +473,8 @@ def main():
         return run_reference(args)
     if args.only_batched:
         return run_batched_only(args)
+    if args.nodecut:
+        return run_nodecut(args)
 
     rank, world, local = dist_env()
     import torch

@@ -169,3 +169,21 @@ def test_shared_state_rules():
     B.close()
     C.close()
     A.close()
+
+
+def test_bench_nodecut_mode():
+    # bench.py's node-cut line: the cavity mesh in 3 parts on this GPU
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--nodecut", "3",
+                          "--steps", "20", "--warmup", "3"], capture_output=True, text=True,
+                         cwd=root, timeout=900)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["form"] == "nodecut" and d["parts"] == 3 and d["steps"] == 20
+    assert d["ms_per_step"] > 0 and d["t_C_ms"] > 0 and d["t_W_ms"] > 0
+    assert len(d["neighbours"]) == 3 and min(d["cut_nodes"]) > 0
+    assert d["rel_err_vs_single_domain"] < 1e-6
