@@ -43,3 +43,24 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_other_ranks_exit_quietly():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_measured_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    # roofline.traffic comes from profiles/force_traffic.txt only while its
+    # sources_sha matches the kernel sources; otherwise null
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    h = b.kernel_sources_hash()
+    p = tmp_path / "traffic.txt"
+    p.write_text("# comment\nsources_sha %s\nmixed_walsh_gen_tc_pair 81.0e6\n" % h)
+    monkeypatch.setattr(b, "TRAFFIC_FILE", str(p))
+    assert b.measured_traffic("mixed_walsh_gen_tc_pair") == 81.0e6
+    assert b.measured_traffic("mixed_tensor_gen_simt_pair") is None
+    p.write_text("sources_sha 0000000000000000\nmixed_walsh_gen_tc_pair 81.0e6\n")
+    assert b.measured_traffic("mixed_walsh_gen_tc_pair") is None
+    monkeypatch.setattr(b, "TRAFFIC_FILE", str(tmp_path / "missing.txt"))
+    assert b.measured_traffic("mixed_walsh_gen_tc_pair") is None
