@@ -470,6 +470,19 @@ struct WhtF {
   float blk[72];   // blocks of T K_p T^T / 8, divided by 8 once more (T T^T = 8 I)
 };
 
+// Shared-memory slot of brick-lattice node q = a + 5 b + 25 c in the Walsh
+// kernel: layer c at 37 c, row-major with a row pitch of 4 for a < 4 and
+// the fifth column after the layer's rows.  Slot mod 16 = (a + 4 b) mod 16
+// (+ the layer's offset), so the 16 nodes that a half-warp's cells read
+// for one corner (a 4 x 4 window of a layer) fall on 16 different pairs of
+// banks at the 24-byte node stride (lattice order puts q and q + 16 on the
+// same banks).
+constexpr int WT_BRICK_SLOTS = 9 * 37;
+__host__ __device__ inline int wt_brick_slot(int q) {
+  const int a = q % 5, b = (q / 5) % 5, c = q / 25;
+  return 37 * c + (a < 4 ? a + 4 * b : 20 + 4 * b);
+}
+
 struct WtLayout {
   uint32_t stage[2], u_off, total;
 };
@@ -477,7 +490,8 @@ __host__ __device__ inline WtLayout wt_layout(int rec_max, int nn_max) {
   WtLayout L;
   uint32_t o = 128;   // 2 record mbarriers
   L.u_off = a16((uint32_t)rec_max);
-  const uint32_t st = a128(L.u_off + 24u * (uint32_t)nn_max);
+  const int slots = nn_max > WT_BRICK_SLOTS ? nn_max : WT_BRICK_SLOTS;
+  const uint32_t st = a128(L.u_off + 24u * (uint32_t)slots);
   L.stage[0] = o; o += st;
   L.stage[1] = o; o += st;
   L.total = o;
@@ -542,12 +556,14 @@ __global__ void __launch_bounds__(WT_THREADS, 6)
   auto issue_gather = [&](int s) {            // all threads
     const Stage S = stage_view(stage_base(s), SL.u_off);
     const int nn = S.hdr[2];
+    const bool brick = S.hdr[3] == 1;
     const uint32_t ub = tc::smem_addr(S.u);
     for (int i = tid; i < nn; i += WT_THREADS) {
       const float *src = u + 6 * (int64_t)S.nodes[i];
-      tc::cp_async8(ub + 24u * i, src);
-      tc::cp_async8(ub + 24u * i + 8u, src + 2);
-      tc::cp_async8(ub + 24u * i + 16u, src + 4);
+      const uint32_t d = ub + 24u * (uint32_t)(brick ? wt_brick_slot(i) : i);
+      tc::cp_async8(d, src);
+      tc::cp_async8(d + 8u, src + 2);
+      tc::cp_async8(d + 16u, src + 4);
     }
     tc::cp_async_commit();
   };
@@ -588,10 +604,13 @@ __global__ void __launch_bounds__(WT_THREADS, 6)
     float o[3][8];
     if (fc < ncell) {
       uint32_t lk[8];
-      if (brick) {   // lattice node index a + 5 b + 25 c
-        const int b0 = (fc & 3) + 5 * ((fc >> 2) & 3) + 25 * (fc >> 4);
+      if (brick) {   // wt_brick_slot of lattice node (x + dx) + 5 (y + dy) + 25 (z + dz)
+        const int x = fc & 3;
+        const int b0 = x + 4 * ((fc >> 2) & 3) + 37 * (fc >> 4);
+        const int sx = x < 3 ? 1 : 17;   // the +x corner: next column, or the layer's fifth
 #pragma unroll
-        for (int k = 0; k < 8; ++k) lk[k] = (uint32_t)(b0 + (k & 1) + 5 * ((k >> 1) & 1) + 25 * (k >> 2));
+        for (int k = 0; k < 8; ++k)
+          lk[k] = (uint32_t)(b0 + (k & 1) * sx + 4 * ((k >> 1) & 1) + 37 * (k >> 2));
       } else {
         const uint4 Lw = *reinterpret_cast<const uint4 *>(S.lid + 8 * fc);
         const uint32_t w4[4] = {Lw.x, Lw.y, Lw.z, Lw.w};
