@@ -470,6 +470,68 @@ struct WhtF {
   float blk[72];   // blocks of T K_p T^T / 8, divided by 8 once more (T T^T = 8 I)
 };
 
+// Local order of a list tile's nodes (host side).  A half-warp of the
+// force kernels' threads reads, for one corner, the node pairs of 16 cells
+// at a 24-byte stride: nodes whose local indices agree mod 16 share a pair
+// of shared-memory banks.  The order keeps the indices a permutation of
+// 0 .. nn-1 and gives each node the residue mod 16 that clashes least with
+// the residues already taken in the (half-warp, corner) sets it belongs to
+// (nodes in the most sets first); lid, the incidence lists and the node
+// list are renumbered to match.
+inline void bank_aware_order(size_t nc, std::vector<int32_t> &nodes, std::vector<uint16_t> &lid,
+                             std::vector<uint16_t> &offs, std::vector<uint16_t> &inc) {
+  const int nn = (int)nodes.size();
+  int cap[16] = {0};
+  for (int j = 0; j < nn; ++j) cap[j & 15]++;
+  std::vector<std::vector<int>> sets((size_t)nn);   // (half-warp, corner) set ids per node
+  for (size_t c = 0; c < nc; ++c)
+    for (int k = 0; k < 8; ++k) sets[lid[c * 8 + k]].push_back((int)(c / 16) * 8 + k);
+  std::vector<uint32_t> taken(((nc + 15) / 16) * 8, 0u);   // bit r: residue r used in the set
+  std::vector<int> ord((size_t)nn);
+  for (int i = 0; i < nn; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(),
+                   [&](int a, int b) { return sets[a].size() > sets[b].size(); });
+  std::vector<int> res((size_t)nn, 0);
+  for (int i : ord) {
+    int best = -1, bcost = 1 << 30;
+    for (int r = 0; r < 16; ++r) {
+      if (!cap[r]) continue;
+      int cost = 0;
+      for (int sid : sets[i]) cost += (int)((taken[sid] >> r) & 1u);
+      if (cost < bcost || (cost == bcost && cap[r] > cap[best])) {
+        best = r;
+        bcost = cost;
+      }
+    }
+    res[i] = best;
+    cap[best]--;
+    for (int sid : sets[i]) taken[sid] |= 1u << best;
+  }
+  int next[16];
+  for (int r = 0; r < 16; ++r) next[r] = r;
+  std::vector<int> perm((size_t)nn), inv((size_t)nn);
+  for (int i = 0; i < nn; ++i) {
+    perm[i] = next[res[i]];
+    next[res[i]] += 16;
+    inv[perm[i]] = i;
+  }
+  std::vector<int32_t> nodes2((size_t)nn);
+  for (int i = 0; i < nn; ++i) nodes2[perm[i]] = nodes[i];
+  for (auto &l : lid) l = (uint16_t)perm[l];
+  std::vector<uint16_t> offs2, inc2;
+  offs2.reserve(offs.size());
+  inc2.reserve(inc.size());
+  for (int j = 0; j < nn; ++j) {
+    offs2.push_back((uint16_t)inc2.size());
+    const int o = inv[j];
+    for (int q = offs[o]; q < offs[o + 1]; ++q) inc2.push_back(inc[q]);
+  }
+  offs2.push_back((uint16_t)inc2.size());
+  nodes.swap(nodes2);
+  offs.swap(offs2);
+  inc.swap(inc2);
+}
+
 // Shared-memory slot of brick-lattice node q = a + 5 b + 25 c in the Walsh
 // kernel: layer c at 37 c, row-major with a row pitch of 4 for a < 4 and
 // the fifth column after the layer's rows.  Slot mod 16 = (a + 4 b) mod 16
@@ -1642,6 +1704,7 @@ int tc_setup(sbx_ctx *ctx, const std::vector<int32_t> &conn, const std::vector<i
         inc.push_back((uint16_t)v[i].second);
       }
       offs.push_back((uint16_t)inc.size());
+      bank_aware_order(nc, nodes, lid, offs, inc);
       const int nn = (int)nodes.size();
       const RecLayout R = rec_layout((int)nc, nn, 0);
       const size_t at = recs.size();
