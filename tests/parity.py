@@ -3,7 +3,7 @@
 Every parity check compares the CUDA path's result a with the FP64 oracle's
 b over ALL entries in two norms and takes the larger:
 
-* the relative L2 error ||a - b||_2 / ||b||_2 (the survey's reading C13), and
+* the relative L2 error ||a - b||_2 / ||b||_2 over the whole state, and
 * the element-wise error max_i |a_i - b_i| / max_i |b_i|,
 
 so an error confined to a few entries (a rare hanging-node pattern among a
